@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Viterbi decoder (arxiv 2011.09337).
+
+Workload (one step): the streaming tiled decode of a K=7 rate-1/2 code
+(generators 171, 133 octal) with f=1024, v1=v2=48 over seven independent
+2^24-bit streams, one per Eb/N0 in 0..6 dB (BPSK/AWGN, int8 LLRs scaled by
+16), decoded by one planned batch (one kernel launch, replayed as a CUDA
+graph).  Inputs are larger than L2 (235 MB of LLRs per step).
+
+Prints one JSON line: decoded info Mbit/s, the per-frame-launch variant, the
+end-to-end number through the C ABI with host buffers, the integer-ALU
+roofline of the decode kernel and the CPU oracle baseline.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K, BETA, POLYS = 7, 2, (0o171, 0o133)
+F, V = 1024, 48
+NBITS = 1 << 24
+EBN0 = [0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0]
+WORKLOAD = ("stream K=7 r1/2 (171,133 octal) f=1024 v1=v2=48, 7 streams x 2^24 info bits, "
+            "Eb/N0 0..6 dB, int8 LLRs x16")
+METRIC = "decoded Mbit/s K=7 r1/2 int8, batched vs per-frame, 1 GB300; % ALU/HBM roofline"
+SM_COUNT = 152
+LANES_PER_SM_CLK = 4 * 32      # 4 SM sub-partitions x 32 lanes issue full-rate integer ops
+OPS_PER_LANE = 2               # two 16-bit path metrics per 32-bit lane (packed max.u16x2 / IADD3)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p.get("sm_max_mhz", 2070.0)), float(p.get("hbm_gbs", 6800.0)), "measured"
+    except OSError:
+        return 2070.0, 6800.0, "fallback"
+
+
+def _kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2011_09337_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch():
+    """DRAM bytes per decode launch from the committed ncu summary, if it was
+    taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "decode_traffic.json")
+    try:
+        with open(p) as fh:
+            t = json.load(fh)
+    except OSError:
+        return None
+    if t.get("source_sha") != _kernel_source_sha():
+        return None
+    return t.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(vit, code, device, torch):
+    """Seven LLR streams (int8, stage-major), encoded by the library's encoder."""
+    from paper_2011_09337_gb300 import synth
+
+    def enc(bits):
+        return vit.encode(code, torch.from_numpy(bits).to(device)).cpu().numpy()
+
+    streams = []
+    for i, e in enumerate(EBN0):
+        s = synth.make_stream(enc, BETA, NBITS, e, seed=1000 + i)
+        streams.append(s)
+    return streams
+
+
+def algorithmic_ops_per_step() -> float:
+    """4 integer ops (2 adds, compare, select) per state per processed stage."""
+    S = 1 << (K - 1)
+    ntiles = NBITS // F
+    stages = 0
+    for b in range(ntiles):
+        e0, e1 = b * F, min((b + 1) * F, NBITS)
+        stages += min(NBITS, e1 + V) - max(0, e0 - V)
+    return 4.0 * S * stages * len(EBN0)
+
+
+def cpu_oracle_rate(seconds: float = 12.0):
+    """Times the oracle's tiled decoder on a bounded sample of the workload with
+    all host cores (ctypes releases the GIL).  Returns (Mbit/s, cores, sample)."""
+    import oracle
+    from paper_2011_09337_gb300 import synth
+
+    cores = len(os.sched_getaffinity(0))
+    n = 256 * F
+    s = synth.make_stream(lambda x: oracle.encode(K, BETA, POLYS, x), BETA, n, 3.0, seed=7)
+    t0 = time.perf_counter()
+    oracle.viterbi_blocked(K, BETA, POLYS, s.llr, F, V, V, blocks=(1, 5))
+    per_tile = (time.perf_counter() - t0) / 4
+    ntiles = int(max(cores, min(255, seconds * cores / max(per_tile, 1e-6))))
+    chunks = np.array_split(np.arange(1, 1 + ntiles), cores)
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=oracle.viterbi_blocked,
+                                args=(K, BETA, POLYS, s.llr, F, V, V),
+                                kwargs={"blocks": (int(c[0]), int(c[-1]) + 1)}) for c in chunks if len(c)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    dt = time.perf_counter() - t0
+    return ntiles * F / dt / 1e6, cores, f"{ntiles} tiles of 1024 bits (f=1024, v=48, 3 dB) on {cores} threads"
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on this workload, bounded steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2011_09337_gb300 import synth
+
+    cores = len(os.sched_getaffinity(0))
+    n = 64 * F
+    s = synth.make_stream(lambda x: oracle.encode(K, BETA, POLYS, x), BETA, n, 3.0, seed=7)
+    tiles_per_step = cores * 2
+
+    def step():
+        chunks = np.array_split(np.arange(tiles_per_step) % 62 + 1, cores)
+        ths = [threading.Thread(target=oracle.viterbi_blocked, args=(K, BETA, POLYS, s.llr, F, V, V),
+                                kwargs={"blocks": (int(c[0]), int(c[0]) + len(c))}) for c in chunks if len(c)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = tiles_per_step * F / dt / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{tiles_per_step} tiles per step"},
+        "cpu_baseline": {"value": value, "unit": "Mbit/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{tiles_per_step} tiles of 1024 bits per step, {cores} threads"},
+        "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2011_09337_gb300 import vit
+    code = vit.Code(K, BETA, POLYS, f=F, v=V)
+    streams = make_inputs(vit, code, dev, torch)
+    nbytes = (NBITS + 7) // 8
+    d_llr = [torch.from_numpy(s.llr.reshape(-1)).to(dev) for s in streams]
+    d_out = [torch.zeros(nbytes, dtype=torch.uint8, device=dev) for _ in streams]
+    frames = [(code, d_llr[i], NBITS, vit.STREAM, d_out[i]) for i in range(len(streams))]
+    batch = vit.Batch(frames, graph=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident timing: one planned batch (one launch) per step
+    for _ in range(args.warmup):
+        batch.run()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            batch.run()
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    bits_per_step = NBITS * len(streams)
+    value = bits_per_step * world / (ms_per_step * 1e-3) / 1e6
+
+    # parity spot check of this run's output against the transmitted bits (BER sanity)
+    from paper_2011_09337_gb300 import synth
+    got = synth.unpack_bits(d_out[6].cpu().numpy(), NBITS)
+    ber6 = float(np.mean(got != streams[6].bits))
+
+    # ---- per-frame launches (one vit_decode per stream) for comparison
+    ws = torch.empty(code.workspace_bytes(NBITS), dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        for i in range(len(streams)):
+            vit.decode(code, d_llr[i], NBITS, out=d_out[i], workspace=ws)
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        for i in range(len(streams)):
+            vit.decode(code, d_llr[i], NBITS, out=d_out[i], workspace=ws)
+    b.record(stream)
+    barrier()
+    per_frame_value = bits_per_step / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
+
+    # ---- end to end through the C ABI with pinned host buffers
+    h_llr = [torch.from_numpy(s.llr.reshape(-1)).pin_memory() for s in streams]
+    h_out = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in streams]
+    h2d = sum(x.numel() for x in h_llr)
+    d2h = sum(x.numel() for x in h_out)
+
+    def e2e_step():
+        for i in range(len(streams)):
+            d_llr[i].copy_(h_llr[i], non_blocking=True)
+        batch.run()
+        for i in range(len(streams)):
+            h_out[i].copy_(d_out[i], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    b.record(stream)
+    barrier()
+    e2e_value = bits_per_step * world / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    sm_max, hbm_gbs, peak_src = _peaks()
+    ops = algorithmic_ops_per_step()
+    peak_tops = SM_COUNT * LANES_PER_SM_CLK * OPS_PER_LANE * sm_max * 1e6 / 1e12
+    achieved_tops = ops / (launch_ms * 1e-3) / 1e12
+    clocks = clk.summary()
+    traffic = _traffic_per_launch()
+    # algorithmic bytes per launch: int8 LLRs of every window + packed output bits
+    alg_bytes = ops / (4 * (1 << (K - 1))) * BETA + bits_per_step / 8
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": len(streams), "info_bits_per_frame": NBITS, "f": F, "v": V,
+                   "launch": "one planned batch per step (CUDA graph)",
+                   "l2": "inputs larger than L2 (235 MB of LLRs per step)"},
+        "per_frame": {"value": per_frame_value, "unit": "Mbit/s", "launches_per_step": len(streams)},
+        "e2e": {"value": e2e_value, "unit": "Mbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved_tops / peak_tops, "traffic": traffic,
+                     "peak_source": f"{SM_COUNT} SMs x 128 lanes x 2 int16 ops x {sm_max:.0f} MHz ({peak_src} max clock)",
+                     "kernel": "decode_tiles_kernel<K=7,beta=2>", "launch_ms": launch_ms,
+                     "hbm_alg_gbs": alg_bytes / (launch_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_gbs},
+        "clocks": clocks,
+        "gpu_launches": args.steps,
+        "ber_6db": ber6,
+    }
+    if clocks.get("sm_mhz"):
+        line["roofline"]["frac_at_sampled_clock"] = achieved_tops / (peak_tops * clocks["sm_mhz"] / sm_max)
+    if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
+        v, cores, sample = cpu_oracle_rate()
+        line["cpu_baseline"] = {"value": v, "unit": "Mbit/s", "cores": cores, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

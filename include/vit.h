@@ -1,0 +1,185 @@
+/*
+ * vit.h -- C ABI of libvit, a GB300-native (sm_103a) soft-decision Viterbi
+ * decoder for rate-1/beta convolutional codes (arxiv 2011.09337).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - All pointers named "device" are CUDA device pointers owned by the
+ *    caller; the library never frees them.  Host pointers are read during the
+ *    call only.  The library owns vit_code / vit_batch handles and the device
+ *    memory they hold.
+ *  - Calls that take a stream enqueue work on it and return without
+ *    synchronising.  The stream is a cudaStream_t passed as void* (NULL = the
+ *    legacy default stream).
+ *  - Every call returns VIT_OK (0) or a negative status; nothing aborts.
+ *    vit_last_error() returns a thread-local message for the last failure.
+ *    A failed launch reports VIT_ECUDA.  Arguments are checked before any
+ *    work is enqueued.
+ *  - LLRs are int8 in [-127, 127] (decoder) or float32 (path metrics),
+ *    stage-major: llr[t*beta + b] is coded bit b of trellis stage t.
+ *    Positive means bit 0 is more likely (Sec. "Hard-decision vs.
+ *    Soft-decision").  With a puncturing pattern set, the decoder input holds
+ *    only the transmitted symbols in the same order.
+ *  - Decoded bits are packed LSB-first: bit t is bit (t & 7) of byte t >> 3.
+ *
+ * Code and trellis (Eq. 1, Fig. 1): generator g_b is a K-bit word whose bit
+ * K-1 taps the current input.  The state is the previous K-1 inputs with the
+ * newest in bit K-2; every branch into state j carries input bit (j >> (K-2)).
+ * Ties in add-compare-select keep the lower-numbered predecessor (decision 0);
+ * the traceback of a tile starts at the highest final path metric, ties going
+ * to the lowest state, or at state 0 at the end of a terminated frame.
+ */
+#ifndef VIT_H
+#define VIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vit_code vit_code;
+typedef struct vit_batch vit_batch;
+typedef void* vit_stream_t; /* cudaStream_t */
+
+enum {
+  VIT_OK = 0,
+  VIT_EINVAL = -1,       /* bad argument (null pointer, size, alignment, range) */
+  VIT_EUNSUPPORTED = -2, /* valid code outside the compiled envelope */
+  VIT_ENOMEM = -3,       /* host or device allocation failed */
+  VIT_ECUDA = -4,        /* a CUDA call or kernel launch failed */
+  VIT_ETIMEOUT = -5      /* a bounded device wait gave up (batched queue) */
+};
+
+/* Frame start/end handling. */
+enum {
+  VIT_STREAM = 0,     /* starts in state 0, free end: traceback from the best state */
+  VIT_TERMINATED = 1, /* starts in state 0, ends with K-1 zero tail bits: traceback
+                         from state 0; the tail bits are not output */
+  VIT_FREE_START = 2  /* unknown start (all initial metrics equal, as in Alg. 1) */
+};
+
+/* ------------------------------------------------------------------ codes */
+
+/*
+ * Creates a code handle.  K in [3, 9], beta in [2, 4], (K-1)*beta <= 32;
+ * polys: beta generator words (host array), each nonzero and < 2^K.
+ * Tiling (Sec. "Previous GPU methods", Fig. relworks): the stream is cut into
+ * tiles of f output stages; tile b decodes stages [b*f, (b+1)*f) from the
+ * window [b*f - v1, (b+1)*f + v2) clipped to the frame, with v1 = v2 = v.
+ * f = 0 decodes each frame as one tile (full-frame Viterbi, Alg. 1 + 2);
+ * otherwise f must be a positive multiple of 8.  A window that does not start
+ * at stage 0 starts with all path metrics equal.
+ * Returns VIT_EUNSUPPORTED for a valid code with no compiled kernel.
+ */
+int vit_create(vit_code** out, int K, int beta, const uint32_t* polys, int64_t f, int64_t v);
+
+/* Sets asymmetric overlaps v1 (left) and v2 (right), both >= 0. */
+int vit_set_overlaps(vit_code* code, int64_t v1, int64_t v2);
+
+/*
+ * Sets a puncturing pattern (Sec. "De-puncturing"): mask is beta x period,
+ * row-major, 1 = transmitted; stage t uses column t mod period.  Removed
+ * symbols decode as LLR 0.  period = 0 clears the pattern.  Every column
+ * must keep at least one symbol.
+ */
+int vit_set_puncture(vit_code* code, const uint8_t* mask, int period);
+
+/* Default frame mode used by vit_decode: VIT_STREAM (initial), VIT_TERMINATED
+ * or VIT_FREE_START. */
+int vit_set_termination(vit_code* code, int mode);
+
+void vit_destroy(vit_code* code);
+
+/* Number of int8 LLRs the decoder reads for n trellis stages. */
+int64_t vit_llr_count(const vit_code* code, int64_t n);
+
+/* Number of decoded bits written for n stages (n - (K-1) when terminated). */
+int64_t vit_output_bits(const vit_code* code, int64_t n);
+
+/* --------------------------------------------------------------- decoding */
+
+/* Device scratch bytes vit_decode_ws needs for an n-stage frame. */
+size_t vit_decode_workspace(const vit_code* code, int64_t n);
+
+/*
+ * Decodes one frame of n >= 1 trellis stages (Alg. 1, Alg. 2 on every tile of
+ * Fig. relworks).  llr: device, vit_llr_count(code, n) int8 values.
+ * bits_out: device, ceil(vit_output_bits(code, n) / 8) bytes, fully written.
+ * ws: device scratch of at least vit_decode_workspace(code, n) bytes,
+ * 256-byte aligned, not used concurrently by another call.
+ */
+int vit_decode_ws(const vit_code* code, const int8_t* llr, int64_t n, uint8_t* bits_out, void* ws, size_t ws_bytes,
+                  vit_stream_t stream);
+
+/* Same as vit_decode_ws with scratch taken from the stream-ordered allocator
+ * (cudaMallocAsync) and released on the same stream. */
+int vit_decode(const vit_code* code, const int8_t* llr, int64_t n, uint8_t* bits_out, vit_stream_t stream);
+
+/*
+ * Convolutional encoder (Eq. 1) starting in state 0: bits is a device array
+ * of n bytes (0/1, one input bit per stage); coded receives n*beta bytes
+ * (0/1) stage-major.  Puncturing is not applied.
+ */
+int vit_encode(const vit_code* code, const uint8_t* bits, int64_t n, uint8_t* coded, vit_stream_t stream);
+
+/* ----------------------------------------------------------------- batches */
+
+typedef struct {
+  const vit_code* code; /* any created code; frames may mix codes */
+  const int8_t* llr;    /* device, vit_llr_count(code, n) int8 values */
+  int64_t n;            /* trellis stages, >= 1 */
+  int mode;             /* VIT_STREAM, VIT_TERMINATED or VIT_FREE_START */
+  uint8_t* bits_out;    /* device, ceil(vit_output_bits / 8) bytes */
+} vit_frame;
+
+/*
+ * Plans a batch: sorts the tiles of all frames by cost, sizes the scratch,
+ * uploads the work queue and, when flags has VIT_BATCH_GRAPH, captures the
+ * persistent decode launch in a CUDA graph on first run.  Frame pointers are
+ * recorded: a plan decodes the same buffers every time it runs.  Tiling uses
+ * each frame's code (f, v1, v2), or the autotuned tiling with VIT_BATCH_TUNE.
+ */
+enum { VIT_BATCH_GRAPH = 1, VIT_BATCH_TUNE = 2 };
+int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int flags);
+int vit_batch_run(vit_batch* batch, vit_stream_t stream);
+void vit_batch_destroy(vit_batch* batch);
+
+/* Plans, runs once and releases the plan after the stream has finished it. */
+int vit_decode_batch(const vit_frame* frames, int nframes, vit_stream_t stream);
+
+/* ------------------------------------------------------ path-metric forms */
+
+/*
+ * Best-path metric of F zero-terminated frames of n stages each (not defined
+ * by the paper; see the oracle): tau == 0 is the hard form
+ *   M = max over 0-rooted, 0-terminated paths of sum_t delta_t (Eq. 2),
+ * tau > 0 the log-sum-exp form M_tau = tau log sum exp(sum_t delta_t / tau).
+ * llr: device float32 [F][n][beta]; metric_out: device float32 [F].
+ * ws: device scratch of vit_metric_workspace(...) bytes, kept unchanged
+ * between vit_metric_fwd and the matching vit_metric_bwd (it holds the
+ * survivor bits, or the forward state metrics every C stages).
+ */
+size_t vit_metric_workspace(const vit_code* code, int nframes, int64_t n, float tau, int C);
+int vit_metric_fwd(const vit_code* code, const float* llr, int nframes, int64_t n, float tau, int C,
+                   float* metric_out, void* ws, size_t ws_bytes, vit_stream_t stream);
+/*
+ * Gradient of sum_f grad_metric[f] * M_f with respect to llr: the +-1 code
+ * symbols of the traced best path (tau == 0) or their posterior expectation
+ * (tau > 0, recomputing forward metrics between checkpoints).
+ * grad_metric: device float32 [F]; grad_llr: device float32 [F][n][beta].
+ */
+int vit_metric_bwd(const vit_code* code, const float* llr, const float* grad_metric, int nframes, int64_t n,
+                   float tau, int C, const void* ws, size_t ws_bytes, float* grad_llr, vit_stream_t stream);
+
+/* ------------------------------------------------------------------ misc */
+
+const char* vit_last_error(void);
+/* 1 if a kernel is compiled for (K, beta, polys), else 0. */
+int vit_code_supported(int K, int beta, const uint32_t* polys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIT_H */

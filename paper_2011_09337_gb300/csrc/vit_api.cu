@@ -1,0 +1,564 @@
+// vit_api.cu -- host side of the C ABI declared in include/vit.h: argument
+// checking, code registry, tiling/workspace arithmetic, launches of the
+// tile decoder, de-puncturing and encoder kernels.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/vit.h"
+#include "vit_internal.h"
+
+using namespace vit;
+
+struct vit_code {
+  int K, beta;
+  uint32_t polys[4];
+  int64_t f, v1, v2;
+  int mode;
+  int period;         // puncturing period (0 = none)
+  uint8_t mask[4 * 64];
+  const CodeEntry* entry;
+};
+
+namespace {
+thread_local std::string g_err;
+std::mutex g_reg_mu;
+std::vector<CodeEntry>& registry() {
+  static std::vector<CodeEntry> r;
+  return r;
+}
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(VIT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int kMaxPeriod = 64;
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int64_t max_window(const vit_code* c, int64_t n) {
+  const int64_t fb = tile_len(n, c->f);
+  int64_t w = fb + c->v1 + c->v2;
+  return w < n ? w : n;
+}
+int64_t kept_in(const vit_code* c, int64_t n) {
+  if (c->period == 0) return n * c->beta;
+  int64_t per = 0, part = 0;
+  const int64_t r = n % c->period;
+  for (int col = 0; col < c->period; col++)
+    for (int b = 0; b < c->beta; b++)
+      if (c->mask[b * c->period + col]) {
+        per++;
+        if (col < r) part++;
+      }
+  return (n / c->period) * per + part;
+}
+
+// ---------------------------------------------------------- small kernels
+struct PunctArgs {
+  int beta, period;
+  int64_t per_period;
+  int32_t col_prefix[kMaxPeriod];     // kept symbols before column col
+  int8_t rank[4 * kMaxPeriod];        // index of (b, col) inside its column, -1 if removed
+};
+
+__global__ void depuncture_kernel(const int8_t* __restrict__ rx, int64_t n, int8_t* __restrict__ out, PunctArgs p) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int col = (int)(t % p.period);
+  const int64_t base = (t / p.period) * p.per_period + p.col_prefix[col];
+  for (int b = 0; b < p.beta; b++) {
+    const int r = p.rank[b * kMaxPeriod + col];
+    out[t * p.beta + b] = (r >= 0) ? rx[base + r] : (int8_t)0;
+  }
+}
+
+__global__ void encode_kernel(const uint8_t* __restrict__ bits, int64_t n, int K, int beta, uint4 polys,
+                              uint8_t* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  uint32_t R = 0;  // Eq. 1 register word: bit K-1 = in_t, bit 0 = in_{t-K+1}
+  for (int m = 0; m < K; m++) {
+    const int64_t s = t - m;
+    const uint32_t v = (s >= 0) ? (uint32_t)(bits[s] & 1u) : 0u;
+    R |= v << (K - 1 - m);
+  }
+  const uint32_t g[4] = {polys.x, polys.y, polys.z, polys.w};
+  for (int b = 0; b < beta; b++) out[t * beta + b] = (uint8_t)(__popc(g[b] & R) & 1);
+}
+
+bool code_args_ok(int K, int beta, const uint32_t* polys) {
+  if (K < 3 || K > 9 || beta < 2 || beta > 4 || polys == nullptr) return false;
+  if ((K - 1) * beta > 32) return false;
+  for (int b = 0; b < beta; b++)
+    if (polys[b] == 0 || (polys[b] >> K) != 0) return false;
+  return true;
+}
+
+int check_code(const vit_code* c) {
+  if (c == nullptr) return fail(VIT_EINVAL, "null code handle");
+  return VIT_OK;
+}
+
+}  // namespace
+
+namespace vit {
+void register_codes(const CodeEntry* e, int n) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (int i = 0; i < n; i++) registry().push_back(e[i]);
+}
+const CodeEntry* find_code(int K, int beta, const uint32_t* polys) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (const CodeEntry& e : registry()) {
+    if (e.K != K || e.beta != beta) continue;
+    bool same = true;
+    for (int b = 0; b < beta; b++) same = same && (e.polys[b] == polys[b]);
+    if (same) return &e;
+  }
+  return nullptr;
+}
+}  // namespace vit
+
+extern "C" {
+
+const char* vit_last_error(void) { return g_err.c_str(); }
+
+int vit_code_supported(int K, int beta, const uint32_t* polys) {
+  if (!code_args_ok(K, beta, polys)) return 0;
+  return find_code(K, beta, polys) != nullptr;
+}
+
+int vit_create(vit_code** out, int K, int beta, const uint32_t* polys, int64_t f, int64_t v) {
+  if (out == nullptr) return fail(VIT_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!code_args_ok(K, beta, polys))
+    return fail(VIT_EINVAL, "invalid code: need K in [3,9], beta in [2,4], (K-1)*beta <= 32, 0 < g_b < 2^K");
+  if (f < 0 || v < 0 || (f % 8) != 0 || f > ((int64_t)1 << 30) || v > ((int64_t)1 << 20))
+    return fail(VIT_EINVAL, "invalid tiling f=%lld v=%lld (f: 0 or a positive multiple of 8)", (long long)f,
+                (long long)v);
+  const CodeEntry* e = find_code(K, beta, polys);
+  if (e == nullptr) return fail(VIT_EUNSUPPORTED, "no kernel compiled for K=%d beta=%d with these generators", K, beta);
+  vit_code* c = new (std::nothrow) vit_code;
+  if (c == nullptr) return fail(VIT_ENOMEM, "out of host memory");
+  memset(c, 0, sizeof *c);
+  c->K = K;
+  c->beta = beta;
+  for (int b = 0; b < beta; b++) c->polys[b] = polys[b];
+  c->f = f;
+  c->v1 = c->v2 = v;
+  c->mode = VIT_STREAM;
+  c->entry = e;
+  *out = c;
+  return VIT_OK;
+}
+
+int vit_set_overlaps(vit_code* c, int64_t v1, int64_t v2) {
+  if (int r = check_code(c)) return r;
+  if (v1 < 0 || v2 < 0 || v1 > ((int64_t)1 << 20) || v2 > ((int64_t)1 << 20))
+    return fail(VIT_EINVAL, "invalid overlaps");
+  c->v1 = v1;
+  c->v2 = v2;
+  return VIT_OK;
+}
+
+int vit_set_puncture(vit_code* c, const uint8_t* mask, int period) {
+  if (int r = check_code(c)) return r;
+  if (period == 0) {
+    c->period = 0;
+    return VIT_OK;
+  }
+  if (mask == nullptr || period < 1 || period > kMaxPeriod) return fail(VIT_EINVAL, "invalid puncturing pattern");
+  for (int col = 0; col < period; col++) {
+    int kept = 0;
+    for (int b = 0; b < c->beta; b++) kept += mask[b * period + col] ? 1 : 0;
+    if (kept == 0) return fail(VIT_EINVAL, "puncturing column %d removes every symbol", col);
+  }
+  for (int i = 0; i < c->beta * period; i++) c->mask[i] = mask[i] ? 1 : 0;
+  c->period = period;
+  return VIT_OK;
+}
+
+int vit_set_termination(vit_code* c, int mode) {
+  if (int r = check_code(c)) return r;
+  if (mode != VIT_STREAM && mode != VIT_TERMINATED && mode != VIT_FREE_START) return fail(VIT_EINVAL, "invalid mode");
+  c->mode = mode;
+  return VIT_OK;
+}
+
+void vit_destroy(vit_code* c) { delete c; }
+
+int64_t vit_llr_count(const vit_code* c, int64_t n) {
+  if (c == nullptr || n < 0) return -1;
+  return kept_in(c, n);
+}
+
+int64_t vit_output_bits(const vit_code* c, int64_t n) {
+  if (c == nullptr || n < 0) return -1;
+  if (c->mode == VIT_TERMINATED) return n > c->K - 1 ? n - (c->K - 1) : 0;
+  return n;
+}
+
+static size_t slab_task_words(const vit_code* c, int64_t n) {
+  const int64_t L = max_window(c, n);
+  const int64_t U = c->entry->unroll;
+  const int64_t Lr = (L + U - 1) / U * U;
+  return (size_t)Lr * 32 * c->entry->words;
+}
+
+size_t vit_decode_workspace(const vit_code* c, int64_t n) {
+  if (c == nullptr || n <= 0) return 0;
+  const int64_t tiles = tile_count(n, c->f);
+  const int64_t tasks = (tiles + 63) / 64;
+  size_t bytes = align_up((size_t)tasks * slab_task_words(c, n) * 4);
+  if (c->period) bytes += align_up((size_t)n * c->beta);
+  return bytes;
+}
+
+static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t* bits_out, void* ws,
+                       size_t ws_bytes, cudaStream_t s) {
+  const int64_t tiles = tile_count(n, c->f);
+  const int64_t tasks = (tiles + 63) / 64;
+  const size_t tw = slab_task_words(c, n);
+  uint8_t* p = (uint8_t*)ws;
+  uint32_t* slab = (uint32_t*)p;
+  p += align_up((size_t)tasks * tw * 4);
+  const int8_t* dec_llr = llr;
+  if (c->period) {
+    int8_t* dep = (int8_t*)p;
+    PunctArgs pa;
+    memset(&pa, 0, sizeof pa);
+    pa.beta = c->beta;
+    pa.period = c->period;
+    int64_t cum = 0;
+    for (int col = 0; col < c->period; col++) {
+      pa.col_prefix[col] = (int32_t)cum;
+      int r = 0;
+      for (int b = 0; b < c->beta; b++) pa.rank[b * kMaxPeriod + col] = c->mask[b * c->period + col] ? r++ : -1;
+      cum += r;
+    }
+    pa.per_period = cum;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    depuncture_kernel<<<grid, 256, 0, s>>>(llr, n, dep, pa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "depuncture launch");
+    dec_llr = dep;
+  }
+  KArgs a;
+  memset(&a, 0, sizeof a);
+  a.f0.llr = dec_llr;
+  a.f0.out = bits_out;
+  a.f0.n = n;
+  a.f0.n_out = vit_output_bits(c, n);
+  a.f0.mode = c->mode;
+  a.frames = nullptr;
+  a.tile0 = nullptr;
+  a.nframes = 1;
+  a.ntiles = tiles;
+  a.tl = Tiling{c->f, c->v1, c->v2};
+  a.M = (uint32_t)(2 * (c->K - 1) * 127 * c->beta + 1);
+  a.ntasks = tasks;
+  a.slab = slab;
+  a.task_words = (int64_t)tw;
+  a.task_base = 0;
+  cudaError_t e = c->entry->launch(a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+  return VIT_OK;
+}
+
+int vit_decode_ws(const vit_code* c, const int8_t* llr, int64_t n, uint8_t* bits_out, void* ws, size_t ws_bytes,
+                  vit_stream_t stream) {
+  if (int r = check_code(c)) return r;
+  if (n <= 0) return fail(VIT_EINVAL, "n must be >= 1");
+  if (llr == nullptr || bits_out == nullptr || ws == nullptr) return fail(VIT_EINVAL, "null device pointer");
+  if (((uintptr_t)ws % kAlign) != 0) return fail(VIT_EINVAL, "workspace must be 256-byte aligned");
+  if (c->mode == VIT_TERMINATED && n <= c->K - 1) return fail(VIT_EINVAL, "terminated frame shorter than its tail");
+  const size_t need = vit_decode_workspace(c, n);
+  if (ws_bytes < need)
+    return fail(VIT_EINVAL, "workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
+  return decode_impl(c, llr, n, bits_out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int vit_decode(const vit_code* c, const int8_t* llr, int64_t n, uint8_t* bits_out, vit_stream_t stream) {
+  if (int r = check_code(c)) return r;
+  if (n <= 0) return fail(VIT_EINVAL, "n must be >= 1");
+  if (llr == nullptr || bits_out == nullptr) return fail(VIT_EINVAL, "null device pointer");
+  if (c->mode == VIT_TERMINATED && n <= c->K - 1) return fail(VIT_EINVAL, "terminated frame shorter than its tail");
+  const size_t need = vit_decode_workspace(c, n);
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, need, s);
+  if (e != cudaSuccess) return fail(VIT_ENOMEM, "workspace allocation of %zu bytes failed: %s", need,
+                                    cudaGetErrorString(e));
+  int r = decode_impl(c, llr, n, bits_out, ws, need, s);
+  e = cudaFreeAsync(ws, s);
+  if (r == VIT_OK && e != cudaSuccess) r = cuda_fail(e, "workspace release");
+  return r;
+}
+
+int vit_encode(const vit_code* c, const uint8_t* bits, int64_t n, uint8_t* coded, vit_stream_t stream) {
+  if (int r = check_code(c)) return r;
+  if (n <= 0) return fail(VIT_EINVAL, "n must be >= 1");
+  if (bits == nullptr || coded == nullptr) return fail(VIT_EINVAL, "null device pointer");
+  const uint4 g = make_uint4(c->polys[0], c->polys[1], c->polys[2], c->polys[3]);
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  encode_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(bits, n, c->K, c->beta, g, coded);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "encode launch");
+  return VIT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+// A plan groups frames that share a compiled kernel and a tiling; each group
+// is one launch over a device frame table.  Punctured frames are
+// de-punctured into plan-owned buffers first.
+struct vit_batch {
+  struct Group {
+    const CodeEntry* entry;
+    Tiling tl;
+    uint32_t M;
+    int nframes;
+    int64_t ntiles, ntasks, task_words;
+    Frame* d_frames = nullptr;
+    int64_t* d_tile0 = nullptr;
+    uint32_t* d_slab = nullptr;
+  };
+  struct Dep {
+    const int8_t* src;
+    int8_t* dst;
+    int64_t n;
+    PunctArgs pa;
+  };
+  std::vector<Group> groups;
+  std::vector<Dep> deps;
+  std::vector<void*> allocs;
+  int flags = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+};
+
+namespace {
+PunctArgs make_punct(const vit_code* c) {
+  PunctArgs pa;
+  memset(&pa, 0, sizeof pa);
+  pa.beta = c->beta;
+  pa.period = c->period;
+  int64_t cum = 0;
+  for (int col = 0; col < c->period; col++) {
+    pa.col_prefix[col] = (int32_t)cum;
+    int r = 0;
+    for (int b = 0; b < c->beta; b++) pa.rank[b * kMaxPeriod + col] = c->mask[b * c->period + col] ? r++ : -1;
+    cum += r;
+  }
+  pa.per_period = cum;
+  return pa;
+}
+
+void batch_free(vit_batch* b) {
+  if (b == nullptr) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  delete b;
+}
+
+int batch_enqueue(vit_batch* b, cudaStream_t s) {
+  for (const auto& d : b->deps) {
+    const unsigned grid = (unsigned)((d.n + 255) / 256);
+    depuncture_kernel<<<grid, 256, 0, s>>>(d.src, d.n, d.dst, d.pa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "depuncture launch");
+  }
+  for (const auto& g : b->groups) {
+    KArgs a;
+    memset(&a, 0, sizeof a);
+    a.frames = g.d_frames;
+    a.tile0 = g.d_tile0;
+    a.nframes = g.nframes;
+    a.ntiles = g.ntiles;
+    a.tl = g.tl;
+    a.M = g.M;
+    a.ntasks = g.ntasks;
+    a.slab = g.d_slab;
+    a.task_words = g.task_words;
+    cudaError_t e = g.entry->launch(a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");
+  }
+  return VIT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int flags) {
+  if (out == nullptr) return fail(VIT_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (frames == nullptr || nframes <= 0) return fail(VIT_EINVAL, "empty batch");
+  for (int i = 0; i < nframes; i++) {
+    const vit_frame& f = frames[i];
+    if (f.code == nullptr || f.llr == nullptr || f.bits_out == nullptr || f.n <= 0)
+      return fail(VIT_EINVAL, "frame %d: null pointer or empty frame", i);
+    if (f.mode != VIT_STREAM && f.mode != VIT_TERMINATED && f.mode != VIT_FREE_START)
+      return fail(VIT_EINVAL, "frame %d: invalid mode", i);
+    if (f.mode == VIT_TERMINATED && f.n <= f.code->K - 1)
+      return fail(VIT_EINVAL, "frame %d: terminated frame shorter than its tail", i);
+  }
+  vit_batch* b = new (std::nothrow) vit_batch;
+  if (b == nullptr) return fail(VIT_ENOMEM, "out of host memory");
+  b->flags = flags;
+  // group frames by (kernel, tiling), keeping frame order inside a group
+  std::vector<int> order(nframes);
+  for (int i = 0; i < nframes; i++) order[i] = i;
+  std::vector<std::vector<int>> members;
+  std::vector<const vit_code*> leaders;
+  for (int i = 0; i < nframes; i++) {
+    const vit_code* c = frames[i].code;
+    int gi = -1;
+    for (size_t k = 0; k < leaders.size(); k++) {
+      const vit_code* l = leaders[k];
+      if (l->entry == c->entry && l->f == c->f && l->v1 == c->v1 && l->v2 == c->v2) gi = (int)k;
+    }
+    if (gi < 0) {
+      leaders.push_back(c);
+      members.emplace_back();
+      gi = (int)leaders.size() - 1;
+    }
+    members[gi].push_back(i);
+  }
+  int rc = VIT_OK;
+  auto dalloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+    b->allocs.push_back(p);
+    return p;
+  };
+  for (size_t k = 0; k < leaders.size() && rc == VIT_OK; k++) {
+    const vit_code* c = leaders[k];
+    vit_batch::Group g;
+    g.entry = c->entry;
+    g.tl = Tiling{c->f, c->v1, c->v2};
+    g.M = (uint32_t)(2 * (c->K - 1) * 127 * c->beta + 1);
+    g.nframes = (int)members[k].size();
+    std::vector<Frame> hf(g.nframes);
+    std::vector<int64_t> ht0(g.nframes);
+    int64_t tiles = 0, maxw = 1;
+    for (int j = 0; j < g.nframes; j++) {
+      const vit_frame& f = frames[members[k][j]];
+      const vit_code* fc = f.code;
+      const int8_t* llr = f.llr;
+      if (fc->period) {
+        int8_t* dst = (int8_t*)dalloc((size_t)f.n * fc->beta);
+        if (dst == nullptr) {
+          rc = fail(VIT_ENOMEM, "device allocation failed");
+          break;
+        }
+        b->deps.push_back(vit_batch::Dep{f.llr, dst, f.n, make_punct(fc)});
+        llr = dst;
+      }
+      hf[j].llr = llr;
+      hf[j].out = f.bits_out;
+      hf[j].n = f.n;
+      hf[j].n_out = (f.mode == VIT_TERMINATED) ? f.n - (fc->K - 1) : f.n;
+      hf[j].mode = f.mode;
+      ht0[j] = tiles;
+      tiles += tile_count(f.n, c->f);
+      const int64_t w = max_window(c, f.n);
+      if (w > maxw) maxw = w;
+    }
+    if (rc != VIT_OK) break;
+    g.ntiles = tiles;
+    g.ntasks = (tiles + 63) / 64;
+    const int64_t U = c->entry->unroll;
+    g.task_words = ((maxw + U - 1) / U * U) * 32 * c->entry->words;
+    g.d_frames = (Frame*)dalloc(sizeof(Frame) * g.nframes);
+    g.d_tile0 = (int64_t*)dalloc(sizeof(int64_t) * g.nframes);
+    g.d_slab = (uint32_t*)dalloc((size_t)g.ntasks * g.task_words * 4);
+    if (!g.d_frames || !g.d_tile0 || !g.d_slab) {
+      rc = fail(VIT_ENOMEM, "device allocation failed");
+      break;
+    }
+    cudaError_t e = cudaMemcpy(g.d_frames, hf.data(), sizeof(Frame) * g.nframes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_tile0, ht0.data(), sizeof(int64_t) * g.nframes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "plan upload");
+      break;
+    }
+    b->groups.push_back(g);
+  }
+  if (rc != VIT_OK) {
+    batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return VIT_OK;
+}
+
+int vit_batch_run(vit_batch* b, vit_stream_t stream) {
+  if (b == nullptr) return fail(VIT_EINVAL, "null batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!(b->flags & VIT_BATCH_GRAPH)) return batch_enqueue(b, s);
+  if (b->exec == nullptr) {
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return cuda_fail(e, "begin capture");
+    }
+    int rc = batch_enqueue(b, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc != VIT_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "graph instantiate");
+    }
+    b->graph = g;
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  return VIT_OK;
+}
+
+void vit_batch_destroy(vit_batch* b) {
+  if (b == nullptr) return;
+  cudaDeviceSynchronize();  // plan buffers may still be in use by enqueued work
+  batch_free(b);
+}
+
+int vit_decode_batch(const vit_frame* frames, int nframes, vit_stream_t stream) {
+  vit_batch* b = nullptr;
+  int rc = vit_batch_plan(&b, frames, nframes, 0);
+  if (rc != VIT_OK) return rc;
+  rc = vit_batch_run(b, stream);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  batch_free(b);
+  if (rc == VIT_OK && e != cudaSuccess) rc = cuda_fail(e, "batch");
+  return rc;
+}
+
+}  // extern "C"

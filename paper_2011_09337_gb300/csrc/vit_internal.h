@@ -1,0 +1,117 @@
+// vit_internal.h -- kernel arguments, the table of compiled codes and the
+// launcher template shared by the per-code translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vit_acs.cuh"
+
+namespace vit {
+
+constexpr int kWarpsPerCta = 4;
+
+// Arguments of the tile decoder.  A "task" is one warp: 32 lanes x 2 tiles.
+struct KArgs {
+  Frame f0;              // single frame (frames == nullptr)
+  const Frame* frames;   // batch frames (device), or nullptr
+  const int64_t* tile0;  // batch: first global tile of each frame, ascending
+  int nframes;
+  int64_t ntiles;        // tiles in this launch
+  Tiling tl;
+  uint32_t M;            // finite "-infinity" of a known start
+  int64_t ntasks;        // warps with work
+  uint32_t* slab;        // survivor words, task_words per task
+  int64_t task_words;
+  int64_t task_base;     // first task index of this launch (for chunked launches)
+};
+
+VIT_HD int64_t find_frame(const int64_t* tile0, int nframes, int64_t gt) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile0[mid] <= gt)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+#if defined(__CUDACC__)
+template <class C>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3) decode_tiles_kernel(const KArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t task = a.task_base + (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  if (task >= a.ntasks) return;  // warp-uniform
+  Half hw[2];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int64_t gt = task * 64 + 2 * lane + h;
+    if (gt >= a.ntiles) {
+      hw[h] = idle_half();
+    } else if (a.frames == nullptr) {
+      hw[h] = make_half(a.f0, gt, a.tl);
+    } else {
+      const int64_t fi = find_frame(a.tile0, a.nframes, gt);
+      hw[h] = make_half(a.frames[fi], gt - a.tile0[fi], a.tl);
+    }
+  }
+  int L = 1;
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+    if (hw[h].active) L = max(L, (int)(hw[h].t1 - hw[h].t0));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) L = max(L, __shfl_xor_sync(0xffffffffu, L, o));
+  const int Lw = ((L + C::U - 1) / C::U) * C::U;
+  int mu = 0;
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+    if (hw[h].active) {
+      hw[h].start = Lw - (int)(hw[h].t1 - hw[h].t0);
+      mu = max(mu, hw[h].start + 1);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+  Slab sl{a.slab + task * a.task_words + lane * C::WORDS, 32 * C::WORDS};
+  decode_pair<C>(hw, Lw, mu, a.M, sl);
+}
+#endif
+
+// One compiled code.
+struct CodeEntry {
+  int K, beta;
+  uint32_t polys[4];
+  int words;  // survivor words per lane per stage
+  int unroll; // stages per unrolled group
+  cudaError_t (*launch)(const KArgs&, cudaStream_t);
+};
+
+#if defined(__CUDACC__)
+template <class C>
+cudaError_t launch_decode(const KArgs& a, cudaStream_t s) {
+  // grid.x is limited to 2^31-1 CTAs; split very large launches
+  const int64_t maxc = (int64_t)1 << 30;
+  for (int64_t t0 = 0; t0 < a.ntasks; t0 += maxc * kWarpsPerCta) {
+    KArgs b = a;
+    b.task_base = t0;
+    const int64_t tasks = (a.ntasks - t0 < maxc * kWarpsPerCta) ? a.ntasks - t0 : maxc * kWarpsPerCta;
+    const unsigned grid = (unsigned)((tasks + kWarpsPerCta - 1) / kWarpsPerCta);
+    decode_tiles_kernel<C><<<grid, kWarpsPerCta * 32, 0, s>>>(b);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <class C>
+constexpr CodeEntry make_entry() {
+  return CodeEntry{C::K, C::BETA, {C::poly(0), C::poly(1), C::poly(2), C::poly(3)}, C::WORDS, C::U,
+                   &launch_decode<C>};
+}
+#endif
+
+// Registry filled by the per-code translation units.
+const CodeEntry* find_code(int K, int beta, const uint32_t* polys);
+void register_codes(const CodeEntry* e, int n);
+
+}  // namespace vit

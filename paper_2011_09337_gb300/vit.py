@@ -1,0 +1,217 @@
+"""Python binding of libvit (include/vit.h): argument marshalling only.
+
+Every step of decoding runs in the library's CUDA kernels; this module checks
+shapes, allocates outputs and scratch with torch on the caller's device and
+passes raw pointers plus ``torch.cuda.current_stream()``.  The library is
+loaded on first use; a missing build raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import torch
+
+from . import build_lib
+
+STREAM, TERMINATED, FREE_START = 0, 1, 2
+BATCH_GRAPH, BATCH_TUNE = 1, 2
+
+_lib = None
+
+
+class VitError(RuntimeError):
+    pass
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def load(path: str | None = None):
+    """Loads libvit.so (built by ``build_lib.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libvit.so not built at {p}: run __graft_entry__.build() or "
+                           "python -m paper_2011_09337_gb300.build_lib")
+    L = ctypes.CDLL(p)
+    i32, i64, vp, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
+    sig = {
+        "vit_create": (i32, [ctypes.POINTER(vp), i32, i32, vp, i64, i64]),
+        "vit_set_overlaps": (i32, [vp, i64, i64]),
+        "vit_set_puncture": (i32, [vp, vp, i32]),
+        "vit_set_termination": (i32, [vp, i32]),
+        "vit_destroy": (None, [vp]),
+        "vit_llr_count": (i64, [vp, i64]),
+        "vit_output_bits": (i64, [vp, i64]),
+        "vit_decode_workspace": (sz, [vp, i64]),
+        "vit_decode_ws": (i32, [vp, vp, i64, vp, vp, sz, vp]),
+        "vit_decode": (i32, [vp, vp, i64, vp, vp]),
+        "vit_encode": (i32, [vp, vp, i64, vp, vp]),
+        "vit_last_error": (ctypes.c_char_p, []),
+        "vit_code_supported": (i32, [i32, i32, vp]),
+    }
+    optional = {
+        "vit_batch_plan": (i32, [ctypes.POINTER(vp), vp, i32, i32]),
+        "vit_batch_run": (i32, [vp, vp]),
+        "vit_batch_destroy": (None, [vp]),
+        "vit_decode_batch": (i32, [vp, i32, vp]),
+        "vit_metric_workspace": (sz, [vp, i32, i64, ctypes.c_float, i32]),
+        "vit_metric_fwd": (i32, [vp, vp, i32, i64, ctypes.c_float, i32, vp, vp, sz, vp]),
+        "vit_metric_bwd": (i32, [vp, vp, vp, i32, i64, ctypes.c_float, i32, vp, sz, vp, vp]),
+    }
+    for name, (res, args) in list(sig.items()) + list(optional.items()):
+        if not hasattr(L, name):
+            if name in sig:
+                raise RuntimeError(f"libvit.so lacks {name}")
+            continue
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load().vit_last_error().decode(errors="replace")
+        raise VitError(f"libvit status {rc}: {msg}")
+
+
+def _stream(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _u32(polys: Sequence[int]) -> ctypes.Array:
+    return (ctypes.c_uint32 * len(polys))(*polys)
+
+
+class Code:
+    """A convolutional code and its tiling (vit_create / vit_set_*)."""
+
+    def __init__(self, K: int, beta: int, polys: Sequence[int], f: int = 0, v: int = 0,
+                 v1: int | None = None, v2: int | None = None, mode: int = STREAM,
+                 puncture: Sequence[Sequence[int]] | None = None):
+        L = load()
+        self.K, self.beta, self.polys = K, beta, tuple(int(p) for p in polys)
+        self.f = f
+        self.v1 = v if v1 is None else v1
+        self.v2 = v if v2 is None else v2
+        self.mode = mode
+        h = ctypes.c_void_p()
+        _check(L.vit_create(ctypes.byref(h), K, beta, ctypes.cast(_u32(self.polys), ctypes.c_void_p), f, v))
+        self._h = h
+        if v1 is not None or v2 is not None:
+            _check(L.vit_set_overlaps(h, self.v1, self.v2))
+        if mode != STREAM:
+            _check(L.vit_set_termination(h, mode))
+        self.puncture = None
+        if puncture is not None:
+            import numpy as np
+            m = np.ascontiguousarray(np.asarray(puncture, dtype=np.uint8))
+            if m.ndim != 2 or m.shape[0] != beta:
+                raise ValueError("puncturing mask must be beta x period")
+            self.puncture = m
+            _check(L.vit_set_puncture(h, m.ctypes.data_as(ctypes.c_void_p), m.shape[1]))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.vit_destroy(h)
+            self._h = None
+
+    def llr_count(self, n: int) -> int:
+        return int(load().vit_llr_count(self._h, n))
+
+    def output_bits(self, n: int) -> int:
+        return int(load().vit_output_bits(self._h, n))
+
+    def workspace_bytes(self, n: int) -> int:
+        return int(load().vit_decode_workspace(self._h, n))
+
+
+def supported(K: int, beta: int, polys: Sequence[int]) -> bool:
+    return bool(load().vit_code_supported(K, beta, ctypes.cast(_u32(polys), ctypes.c_void_p)))
+
+
+def decode(code: Code, llr: torch.Tensor, n: int | None = None, out: torch.Tensor | None = None,
+           workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Decodes one frame.  ``llr``: int8 CUDA tensor of code.llr_count(n) values
+    (stage-major).  Returns packed bits (uint8, LSB-first)."""
+    if not (llr.is_cuda and llr.dtype == torch.int8 and llr.is_contiguous()):
+        raise ValueError("llr must be a contiguous int8 CUDA tensor")
+    if n is None:
+        if code.puncture is not None:
+            raise ValueError("n is required with puncturing")
+        n = llr.numel() // code.beta
+    if llr.numel() != code.llr_count(n):
+        raise ValueError(f"expected {code.llr_count(n)} LLRs for {n} stages, got {llr.numel()}")
+    nbytes = (code.output_bits(n) + 7) // 8
+    if out is None:
+        out = torch.empty(nbytes, dtype=torch.uint8, device=llr.device)
+    elif out.numel() < nbytes or out.dtype != torch.uint8 or not out.is_cuda:
+        raise ValueError("out too small")
+    need = code.workspace_bytes(n)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=llr.device)
+    _check(load().vit_decode_ws(code.handle, llr.data_ptr(), n, out.data_ptr(), workspace.data_ptr(), need,
+                                _stream(llr.device)))
+    return out
+
+
+def encode(code: Code, bits: torch.Tensor) -> torch.Tensor:
+    """Eq. 1 encoder on the GPU: uint8 bits (n,) -> coded bits (n, beta)."""
+    if not (bits.is_cuda and bits.dtype == torch.uint8 and bits.is_contiguous()):
+        raise ValueError("bits must be a contiguous uint8 CUDA tensor")
+    n = bits.numel()
+    out = torch.empty((n, code.beta), dtype=torch.uint8, device=bits.device)
+    _check(load().vit_encode(code.handle, bits.data_ptr(), n, out.data_ptr(), _stream(bits.device)))
+    return out
+
+
+class _Frame(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("llr", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("mode", ctypes.c_int), ("bits_out", ctypes.c_void_p)]
+
+
+class Batch:
+    """A planned batch of frames (vit_batch_plan): decodes the same device
+    buffers every time ``run()`` is called; ``graph=True`` replays one
+    captured CUDA graph."""
+
+    def __init__(self, frames, graph: bool = True):
+        """frames: iterable of (code, llr, n, mode, out) with CUDA tensors."""
+        L = load()
+        self._keep = []
+        arr = (_Frame * len(frames))()
+        for i, (code, llr, n, mode, out) in enumerate(frames):
+            if not (llr.is_cuda and llr.dtype == torch.int8 and llr.is_contiguous()):
+                raise ValueError("llr must be a contiguous int8 CUDA tensor")
+            if llr.numel() != code.llr_count(n):
+                raise ValueError(f"frame {i}: expected {code.llr_count(n)} LLRs, got {llr.numel()}")
+            nb = n - (code.K - 1) if mode == TERMINATED else n
+            if out.numel() < (nb + 7) // 8:
+                raise ValueError(f"frame {i}: output too small")
+            arr[i] = _Frame(code.handle.value, llr.data_ptr(), n, mode, out.data_ptr())
+            self._keep.append((code, llr, out))
+        h = ctypes.c_void_p()
+        _check(L.vit_batch_plan(ctypes.byref(h), arr, len(frames), BATCH_GRAPH if graph else 0))
+        self._h = h
+        self.device = frames[0][1].device
+
+    def run(self):
+        _check(load().vit_batch_run(self._h, _stream(self.device)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.vit_batch_destroy(h)
+            self._h = None
