@@ -16,15 +16,6 @@
 
 using namespace vit;
 
-struct vit_code {
-  int K, beta;
-  uint32_t polys[4];
-  int64_t f, v1, v2;
-  int mode;
-  int period;         // puncturing period (0 = none)
-  uint8_t mask[4 * 64];
-  const CodeEntry* entry;
-};
 
 namespace {
 thread_local std::string g_err;
@@ -118,6 +109,15 @@ int check_code(const vit_code* c) {
 }  // namespace
 
 namespace vit {
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
 void register_codes(const CodeEntry* e, int n) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   for (int i = 0; i < n; i++) registry().push_back(e[i]);

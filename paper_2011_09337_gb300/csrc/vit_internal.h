@@ -115,3 +115,19 @@ const CodeEntry* find_code(int K, int beta, const uint32_t* polys);
 void register_codes(const CodeEntry* e, int n);
 
 }  // namespace vit
+
+// The opaque handle of include/vit.h.
+struct vit_code {
+  int K, beta;
+  uint32_t polys[4];
+  int64_t f, v1, v2;
+  int mode;
+  int period;  // puncturing period (0 = none)
+  uint8_t mask[4 * 64];
+  const vit::CodeEntry* entry;
+};
+
+namespace vit {
+// Sets the thread-local message returned by vit_last_error and returns code.
+int set_error(int code, const char* fmt, ...);
+}  // namespace vit

@@ -1,0 +1,113 @@
+"""CPU checks of the C ABI library: it loads, exports every entry point that
+include/vit.h declares, and its host-side argument checking, tiling and
+workspace arithmetic behave as documented.  No compute call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2011_09337_gb300 import build_lib
+    path = build_lib.build()
+    L = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    L.vit_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp, i64, i64]
+    L.vit_last_error.restype = ctypes.c_char_p
+    L.vit_llr_count.argtypes = [vp, i64]
+    L.vit_llr_count.restype = i64
+    L.vit_output_bits.argtypes = [vp, i64]
+    L.vit_output_bits.restype = i64
+    L.vit_decode_workspace.argtypes = [vp, i64]
+    L.vit_decode_workspace.restype = ctypes.c_size_t
+    L.vit_set_puncture.argtypes = [vp, vp, ctypes.c_int]
+    L.vit_set_termination.argtypes = [vp, ctypes.c_int]
+    L.vit_set_overlaps.argtypes = [vp, i64, i64]
+    L.vit_destroy.argtypes = [vp]
+    L.vit_code_supported.argtypes = [ctypes.c_int, ctypes.c_int, vp]
+    L.vit_decode_ws.argtypes = [vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
+    return L
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "vit.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vit_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "vit_decode" in names and "vit_metric_bwd" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def _u32(*p):
+    return ctypes.cast((ctypes.c_uint32 * len(p))(*p), ctypes.c_void_p)
+
+
+def _create(lib, K, beta, polys, f, v):
+    h = ctypes.c_void_p()
+    rc = lib.vit_create(ctypes.byref(h), K, beta, _u32(*polys), f, v)
+    return rc, h
+
+
+def test_create_validates_arguments(lib):
+    rc, h = _create(lib, 7, 2, (0o171, 0o133), 1024, 48)
+    assert rc == 0 and h.value
+    lib.vit_destroy(h)
+    # invalid codes and tilings
+    for args in ((2, 2, (3, 1), 0, 0), (10, 2, (1, 1), 0, 0), (7, 5, (1, 1, 1, 1, 1), 0, 0),
+                 (7, 2, (0, 0o133), 0, 0), (7, 2, (0o400, 0o133), 0, 0), (9, 5, (1,) * 5, 0, 0),
+                 (7, 2, (0o171, 0o133), 1000, 48), (7, 2, (0o171, 0o133), -8, 0), (7, 2, (0o171, 0o133), 8, -1)):
+        rc, h = _create(lib, *args)
+        assert rc == -1 and not h.value, args
+        assert lib.vit_last_error()
+    # a valid code with no compiled kernel
+    rc, h = _create(lib, 7, 2, (0o165, 0o133), 0, 0)
+    assert rc == -2 and b"no kernel" in lib.vit_last_error()
+    assert lib.vit_code_supported(7, 2, _u32(0o171, 0o133)) == 1
+    assert lib.vit_code_supported(7, 2, _u32(0o165, 0o133)) == 0
+
+
+def test_counts_and_workspace(lib):
+    rc, h = _create(lib, 7, 2, (0o171, 0o133), 1024, 48)
+    assert rc == 0
+    assert lib.vit_llr_count(h, 1000) == 2000
+    assert lib.vit_output_bits(h, 1000) == 1000
+    assert lib.vit_set_termination(h, 1) == 0
+    assert lib.vit_output_bits(h, 1000) == 994
+    assert lib.vit_set_termination(h, 7) == -1
+    # workspace: ceil(tiles / 64) tasks x (window rounded to 6) x 32 lanes x 16 bytes
+    n = 1 << 20
+    tiles = n // 1024
+    want = ((tiles + 63) // 64) * 1122 * 32 * 16
+    assert lib.vit_decode_workspace(h, n) == (want + 255) // 256 * 256
+    # rate-3/4 puncturing [110;101]: 4 symbols per 3 stages
+    mask = (ctypes.c_uint8 * 6)(1, 1, 0, 1, 0, 1)
+    assert lib.vit_set_puncture(h, ctypes.cast(mask, ctypes.c_void_p), 3) == 0
+    assert lib.vit_llr_count(h, 3000) == 4000
+    assert lib.vit_llr_count(h, 3001) == 4002
+    assert lib.vit_llr_count(h, 3002) == 4003
+    bad = (ctypes.c_uint8 * 6)(1, 0, 0, 1, 0, 0)
+    assert lib.vit_set_puncture(h, ctypes.cast(bad, ctypes.c_void_p), 3) == -1
+    assert lib.vit_set_overlaps(h, 10, -1) == -1
+    lib.vit_destroy(h)
+
+
+def test_decode_rejects_bad_arguments_before_any_launch(lib):
+    rc, h = _create(lib, 7, 2, (0o171, 0o133), 1024, 48)
+    fake = ctypes.c_void_p(0x1000)
+    # null pointers, empty frame, unaligned or short workspace: all refused on the host
+    assert lib.vit_decode_ws(h, None, 100, fake, fake, 1 << 30, None) == -1
+    assert lib.vit_decode_ws(h, fake, 0, fake, fake, 1 << 30, None) == -1
+    assert lib.vit_decode_ws(h, fake, 100, fake, ctypes.c_void_p(0x1001), 1 << 30, None) == -1
+    assert lib.vit_decode_ws(h, fake, 100, fake, fake, 16, None) == -1
+    assert b"workspace too small" in lib.vit_last_error()
+    assert lib.vit_decode_ws(None, fake, 100, fake, fake, 1 << 30, None) == -1
+    lib.vit_destroy(h)
