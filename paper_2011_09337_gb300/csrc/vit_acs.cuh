@@ -10,20 +10,19 @@
 // rate) performs both compare-selects.  All 2^(K-1) states of the pair live in
 // the lane's registers (K <= 7), so add-compare-select needs no data exchange.
 //
-// In-place trellis.  Register ("slot") s holds state rotr(s, r) after r stages
-// (rotation over K-1 bits).  The radix-2 butterfly of Eq. 3 then reads and
-// writes the same two slots, which differ in bit r mod (K-1); unrolling K-1
-// stages turns the permutation into register renaming.  The decoded bit of a
-// stage is the pair bit of the traced slot, and the predecessor slot replaces
-// that bit with the survivor decision (Eq. 4), so traceback (Alg. 2) is a
-// bit-field insert per stage.
+// Trellis layout.  Register j holds state j.  A radix-2 butterfly (Eq. 3)
+// reads states 2x and 2x+1 and writes states x and x + S/2 into a second
+// register array; the next stage reads that array the same way, so two
+// unrolled stages (array A -> B -> A) cover the whole permutation with
+// register renaming and a small loop body.  Traceback (Alg. 2) follows
+// predecessor (2j + decision) mod S and outputs bit K-2 of each state.
 //
 // Survivor decisions.  decision = [odd-predecessor candidate > even one]
 // (ties keep the lower predecessor).  E = X_even - X_odd + 2^15 as one 32-bit
 // integer has bit 15 = NOT decision(tile A) and bit 31 = decision(tile B).
 // prmt in sign-replicate mode turns two E words into four 0x00/0xff bytes and
 // a masked OR places them in the stage's survivor words: bit 16*h + pos(s) of
-// word wd(s) is the (A-inverted) decision of slot s, tile h.
+// word wd(j) is the (A-inverted) decision of state j, tile h.
 #pragma once
 #include <stdint.h>
 
@@ -50,19 +49,24 @@ VIT_CX uint32_t rotr_w(uint32_t x, int r, int w) {
   return (r % w) == 0 ? x : (((x >> (r % w)) | (x << (w - (r % w)))) & ((1u << w) - 1u));
 }
 
+constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+
 // A rate-1/beta code with constraint length K and generators G0..G3 (bit K-1
 // taps the current input, Eq. 1).
 template <int K_, int B_, uint32_t G0, uint32_t G1, uint32_t G2 = 0, uint32_t G3 = 0>
 struct Code {
   static constexpr int K = K_, BETA = B_, KM1 = K_ - 1, S = 1 << (K_ - 1);
-  static constexpr int NS = S;                       // slots per lane (lane-local trellis)
+  static constexpr int NS = S < 64 ? S : 64;            // states (slots) per lane
+  static constexpr int G = S / NS;                      // lanes per tile pair
+  static constexpr int NSB = ilog2c(NS);                // slot bits held in registers
   static constexpr int WORDS = NS >= 16 ? NS / 16 : 1;  // survivor words per lane per stage
   static constexpr int HALFP = NS >= 16 ? 8 : NS / 2;   // prmt partner offset
-  static constexpr int ND = 1 << (B_ - 1);           // branch-metric magnitudes per stage
-  // stages per unrolled group: a multiple of K-1 (rotation period)
-  static constexpr int U = KM1;
-  // renormalise every RN groups (<= 16 stages keeps every field in range)
-  static constexpr int RN = (12 / U) > 0 ? (12 / U) : 1;
+  static constexpr int ND = 1 << (B_ - 1);              // branch-metric magnitudes per stage
+  // stages per unrolled group: two alternating register arrays (one lane per
+  // pair) or the K-1 phases of the rotating slot map (several lanes per pair)
+  static constexpr int U = (G == 1) ? 2 : KM1;
+  // renormalise every RN groups (at most 16 stages keeps every field in range)
+  static constexpr int RN = (G == 1) ? 6 : (16 / KM1);
   static VIT_CX uint32_t poly(int b) { return b == 0 ? G0 : b == 1 ? G1 : b == 2 ? G2 : G3; }
   // branch output alpha_out for register word R (Eq. 1), bit b = coded bit b
   static VIT_CX uint32_t aout(uint32_t R) {
@@ -70,8 +74,13 @@ struct Code {
     for (int b = 0; b < B_; b++) o |= (uint32_t)cpar(poly(b) & R) << b;
     return o;
   }
-  static_assert(K_ >= 3 && K_ <= 7, "lane-local trellis holds at most 64 states");
+  // every generator taps both the current and the oldest input: the four
+  // branches of a butterfly carry +-delta of one pattern
+  static constexpr bool SYMMETRIC = ((G0 & G1 & (B_ > 2 ? G2 : ~0u) & (B_ > 3 ? G3 : ~0u)) & 1u) &&
+                                    ((G0 & G1 & (B_ > 2 ? G2 : ~0u) & (B_ > 3 ? G3 : ~0u)) >> (K_ - 1) & 1u);
+  static_assert(K_ >= 3 && K_ <= 9, "K in [3, 9]");
   static_assert(B_ >= 2 && B_ <= 4, "beta in [2,4]");
+  static_assert(G == 1 || SYMMETRIC, "codes spread over several lanes need the butterfly symmetry");
 };
 
 // ------------------------------------------------------------ primitives
@@ -161,23 +170,24 @@ VIT_HD int surv_pos(int s) {
   return (s & (C::HALFP - 1)) + ((s & C::HALFP) ? 8 : 0);
 }
 
-// One radix-2 butterfly (Eq. 3, Eq. 4): slots a (even predecessor) and
-// b = a | 2^P (odd predecessor) are replaced by the two successors.
-template <class C, int P>
-VIT_HD void butterfly(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND], int a, uint32_t& Ea, uint32_t& Eb) {
-  const int b = a | (1 << P);
-  const uint32_t i0 = rotr_w((uint32_t)a, P, C::KM1);  // even predecessor state in slot a
+// One radix-2 butterfly (Eq. 3, Eq. 4): predecessors 2x (even) and 2x+1
+// (odd) of mi give successors x and x + S/2 in mo, with their decision words.
+template <class C>
+VIT_HD void butterfly(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const uint32_t (&D)[C::ND], int x,
+                      uint32_t& E0, uint32_t& E1) {
+  constexpr int H = C::NS / 2;
+  const uint32_t i0 = 2u * (uint32_t)x;
   const uint32_t c00 = C::aout(i0), c01 = C::aout(i0 | 1u);
   const uint32_t c10 = C::aout(i0 | (uint32_t)C::S), c11 = C::aout(i0 | (uint32_t)C::S | 1u);
-  const uint32_t x00 = add_bm<C>(m[a], D, c00), x01 = add_bm<C>(m[b], D, c01);
-  const uint32_t x10 = add_bm<C>(m[a], D, c10), x11 = add_bm<C>(m[b], D, c11);
-  Ea = x00 - x01 + 0x8000u;
-  Eb = x10 - x11 + 0x8000u;
-  m[a] = vmaxu2(x00, x01);  // successor state (i0 >> 1) lands in slot a
-  m[b] = vmaxu2(x10, x11);  // successor state (i0 >> 1) + S/2 lands in slot b
+  const uint32_t x00 = add_bm<C>(mi[2 * x], D, c00), x01 = add_bm<C>(mi[2 * x + 1], D, c01);
+  const uint32_t x10 = add_bm<C>(mi[2 * x], D, c10), x11 = add_bm<C>(mi[2 * x + 1], D, c11);
+  E0 = x00 - x01 + 0x8000u;
+  E1 = x10 - x11 + 0x8000u;
+  mo[x] = vmaxu2(x00, x01);
+  mo[x + H] = vmaxu2(x10, x11);
 }
 
-// Places the decisions of slots s and s + HALFP (both tiles) into the
+// Places the decisions of states s and s + HALFP (both tiles) into the
 // stage's survivor words.
 template <class C>
 VIT_HD void gather2(uint32_t (&w)[C::WORDS], int s, uint32_t Es, uint32_t Ep) {
@@ -185,38 +195,38 @@ VIT_HD void gather2(uint32_t (&w)[C::WORDS], int s, uint32_t Es, uint32_t Ep) {
   w[surv_word<C>(s)] |= t & (0x01010101u << (s & (C::HALFP - 1)));
 }
 
-// One add-compare-select stage for phase P = stage mod (K-1).  Butterflies
-// are visited so that the two slots each prmt combines (s, s + HALFP) are
-// finished together, which keeps few decision words live.
-template <class C, int P>
-VIT_HD void acs_stage(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND], uint32_t (&w)[C::WORDS]) {
-  constexpr int H = C::HALFP;
-  constexpr int B = 1 << P;
+// One add-compare-select stage from mi to mo.  Butterflies are visited so
+// that the two states each prmt combines (s, s + HALFP) are finished
+// together, which keeps few decision words live.
+template <class C>
+VIT_HD void acs_stage(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const uint32_t (&D)[C::ND],
+                      uint32_t (&w)[C::WORDS]) {
+  constexpr int H = C::NS / 2;
+  constexpr int HP = C::HALFP;
 #pragma unroll
   for (int k = 0; k < C::WORDS; k++) w[k] = 0u;
-  if constexpr (B == H) {
-    // the butterfly partner is the prmt partner
+  if constexpr (H == HP) {
+    // the two successors of a butterfly are a prmt pair
 #pragma unroll
-    for (int a = 0; a < C::NS; a++) {
-      if (a & B) continue;
-      uint32_t Ea, Eb;
-      butterfly<C, P>(m, D, a, Ea, Eb);
-      gather2<C>(w, a, Ea, Eb);
+    for (int x = 0; x < H; x++) {
+      uint32_t E0, E1;
+      butterfly<C>(mi, mo, D, x, E0, E1);
+      gather2<C>(w, x, E0, E1);
     }
   } else {
 #pragma unroll
-    for (int a = 0; a < C::NS; a++) {
-      if ((a & B) || (a & H)) continue;
-      uint32_t E0, E1, E2, E3;  // slots a, a|B, a|H, a|B|H
-      butterfly<C, P>(m, D, a, E0, E1);
-      butterfly<C, P>(m, D, a | H, E2, E3);
-      gather2<C>(w, a, E0, E2);
-      gather2<C>(w, a | B, E1, E3);
+    for (int x = 0; x < H; x++) {
+      if (x & HP) continue;
+      uint32_t Ea, Eb, Ec, Ed;  // successors x, x+H, x+HP, x+HP+H
+      butterfly<C>(mi, mo, D, x, Ea, Eb);
+      butterfly<C>(mi, mo, D, x + HP, Ec, Ed);
+      gather2<C>(w, x, Ea, Ec);
+      gather2<C>(w, x + H, Eb, Ed);
     }
   }
 }
 
-// Subtracts the metric of slot 0 from every slot (both tiles) and re-biases.
+// Subtracts the metric of state 0 from every state (both tiles) and re-biases.
 template <class C>
 VIT_HD void renorm(uint32_t (&m)[C::NS]) {
   const uint32_t r = m[0];
@@ -301,25 +311,30 @@ struct Slab {
   int64_t stride;
 };
 
+// LLRs of U consecutive stages for both tiles, as sign-extended ints.
 template <class C>
-VIT_HD void load_stage_llr(const Half (&hw)[2], int i, bool masked, int (&lA)[C::BETA], int (&lB)[C::BETA]) {
+struct LlrGroup {
+  int v[C::U][2][C::BETA];
+};
+
+// Loads the LLRs of the U stages starting at iteration i.  Stages before a
+// tile's window start read the window's first stage (always a valid
+// address); masking to zero happens at use.
+template <class C>
+VIT_HD void load_group(const Half (&hw)[2], int i, LlrGroup<C>& g) {
 #pragma unroll
-  for (int h = 0; h < 2; h++) {
-    const bool on = !masked || (i >= hw[h].start);
-    const int64_t t = hw[h].t0 + (int64_t)(i - hw[h].start);
-    const int8_t* p = hw[h].llr + (on ? t : hw[h].t0) * C::BETA;
+  for (int u = 0; u < C::U; u++)
 #pragma unroll
-    for (int b = 0; b < C::BETA; b++) {
-      const int v = (on && hw[h].active) ? ld_s8(p + b) : 0;
-      if (h == 0)
-        lA[b] = v;
-      else
-        lB[b] = v;
+    for (int h = 0; h < 2; h++) {
+      const int it = i + u;
+      const int64_t t = hw[h].t0 + (int64_t)((it > hw[h].start ? it : hw[h].start) - hw[h].start);
+      const int8_t* p = hw[h].llr + t * C::BETA;
+#pragma unroll
+      for (int b = 0; b < C::BETA; b++) g.v[u][h][b] = hw[h].active ? ld_s8(p + b) : 0;
     }
-  }
 }
 
-VIT_HD void store_words4(uint32_t* p, const uint32_t* w, int n) {
+VIT_HD void store_words(uint32_t* p, const uint32_t* w, int n) {
 #if defined(__CUDA_ARCH__)
   if (n == 4) {
     *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -333,45 +348,64 @@ VIT_HD void store_words4(uint32_t* p, const uint32_t* w, int n) {
   for (int k = 0; k < n; k++) p[k] = w[k];
 }
 
-// Forward procedure over the window of both tiles: Lw iterations (a multiple
-// of U), survivor words to the slab.  masked_until: iterations below it may
-// contain pre-start stages of some lane of the warp.
-template <class C, int P>
-VIT_HD void fwd_one(uint32_t (&m)[C::NS], const Half (&hw)[2], int i, bool masked, uint32_t M, Slab sl) {
+template <class C>
+VIT_HD void load_words(const Slab& sl, int i, uint32_t (&w)[C::WORDS]) {
+#if defined(__CUDA_ARCH__)
+  const uint32_t* p = sl.base + (int64_t)i * sl.stride;
+  if constexpr (C::WORDS == 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+  } else if constexpr (C::WORDS == 2) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    w[0] = v.x, w[1] = v.y;
+  } else {
+    w[0] = p[0];
+  }
+#else
+  for (int k = 0; k < C::WORDS; k++) w[k] = sl.base[(int64_t)i * sl.stride + k];
+#endif
+}
+
+// One stage: branch metrics of both tiles (masked before a window's start),
+// the known-start reset, add-compare-select from mi to mo, survivor store.
+template <class C>
+VIT_HD void fwd_stage(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const Half (&hw)[2], int i, bool masked,
+                      uint32_t M, const int (&lv)[2][C::BETA], Slab sl) {
   int lA[C::BETA], lB[C::BETA];
-  load_stage_llr<C>(hw, i, masked, lA, lB);
+#pragma unroll
+  for (int b = 0; b < C::BETA; b++) {
+    lA[b] = lv[0][b];
+    lB[b] = lv[1][b];
+  }
   if (masked) {
-    // a known-start tile begins here: set its initial metrics
+#pragma unroll
+    for (int b = 0; b < C::BETA; b++) {
+      lA[b] = (i >= hw[0].start) ? lA[b] : 0;
+      lB[b] = (i >= hw[1].start) ? lB[b] : 0;
+    }
+    // a known-start tile begins at this stage: set its initial metrics
 #pragma unroll
     for (int h = 0; h < 2; h++)
-      if (hw[h].known && i == hw[h].start) init_half<C>(m, h, true, M);
+      if (hw[h].known && i == hw[h].start) init_half<C>(mi, h, true, M);
   }
   uint32_t D[C::ND];
   stage_bm<C>(lA, lB, D);
   uint32_t w[C::WORDS];
-  acs_stage<C, P>(m, D, w);
-  store_words4(sl.base + (int64_t)i * sl.stride, w, C::WORDS);
+  acs_stage<C>(mi, mo, D, w);
+  store_words(sl.base + (int64_t)i * sl.stride, w, C::WORDS);
 }
 
-template <class C, int P>
-VIT_HD void fwd_group(uint32_t (&m)[C::NS], const Half (&hw)[2], int i0, bool masked, uint32_t M, Slab sl) {
-  if constexpr (P < C::KM1) {
-    fwd_one<C, P>(m, hw, i0 + P, masked, M, sl);
-    fwd_group<C, P + 1>(m, hw, i0, masked, M, sl);
-  }
-}
-
-// Traceback (Alg. 2) of both tiles from the end of the window.
-template <class C, int P>
-VIT_HD void tb_one(int i, const uint32_t (&w)[C::WORDS], int (&s)[2], uint32_t (&acc)[2], const Half (&hw)[2]) {
+// Traceback step (Alg. 2) of both tiles at iteration i.
+template <class C>
+VIT_HD void tb_stage(int i, const uint32_t (&w)[C::WORDS], int (&s)[2], uint32_t (&acc)[2], const Half (&hw)[2]) {
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     const int64_t t = hw[h].t0 + (int64_t)(i - hw[h].start);
-    const int slot = s[h];
-    const uint32_t word = pick_word<C>(w, slot);
-    const uint32_t d = ((word >> (16 * h + surv_pos<C>(slot))) & 1u) ^ (h == 0 ? 1u : 0u);
-    const uint32_t bit = (uint32_t)(slot >> P) & 1u;
-    s[h] = (slot & ~(1 << P)) | (int)(d << P);
+    const int j = s[h];
+    const uint32_t word = pick_word<C>(w, j);
+    const uint32_t d = ((word >> (16 * h + surv_pos<C>(j))) & 1u) ^ (h == 0 ? 1u : 0u);
+    const uint32_t bit = (uint32_t)(j >> (C::K - 2)) & 1u;
+    s[h] = ((j << 1) | (int)d) & (C::S - 1);
     if (hw[h].active && t >= hw[h].e0 && t < hw[h].e1) {
       acc[h] |= bit << (t & 7);
       if ((t & 7) == 0 || t == hw[h].e0) {
@@ -382,67 +416,41 @@ VIT_HD void tb_one(int i, const uint32_t (&w)[C::WORDS], int (&s)[2], uint32_t (
   }
 }
 
-template <class C>
-VIT_HD void load_words(const Slab& sl, int i, uint32_t* w) {
-#if defined(__CUDA_ARCH__)
-  const uint32_t* p = sl.base + (int64_t)i * sl.stride;
-  if (C::WORDS == 4) {
-    const uint4 v = *reinterpret_cast<const uint4*>(p);
-    w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
-    return;
-  }
-  if (C::WORDS == 2) {
-    const uint2 v = *reinterpret_cast<const uint2*>(p);
-    w[0] = v.x, w[1] = v.y;
-    return;
-  }
-  w[0] = p[0];
-#else
-  for (int k = 0; k < C::WORDS; k++) w[k] = sl.base[(int64_t)i * sl.stride + k];
-#endif
-}
-
-// stages of a group go from i0 + K-2 down to i0
-template <class C, int P>
-VIT_HD void tb_group(int i0, const uint32_t (&w)[C::KM1][C::WORDS], int (&s)[2], uint32_t (&acc)[2],
-                     const Half (&hw)[2]) {
-  if constexpr (P < C::KM1) {
-    constexpr int Q = C::KM1 - 1 - P;
-    tb_one<C, Q>(i0 + Q, w[Q], s, acc, hw);
-    tb_group<C, P + 1>(i0, w, s, acc, hw);
-  }
-}
-
-// Decodes the two tiles of one lane.  Lw: iterations (multiple of K-1, at
+// Decodes the two tiles of one lane.  Lw: iterations (a multiple of U, at
 // least every active window length); masked_until: first iteration from which
 // every window of the warp has started.
 template <class C>
 VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t M, Slab sl) {
-  uint32_t m[C::NS];
+  uint32_t ma[C::NS], mb[C::NS];
 #pragma unroll
-  for (int s = 0; s < C::NS; s++) m[s] = 0x80008000u;
-  // tiles that begin at iteration 0 with a known start
+  for (int s = 0; s < C::NS; s++) ma[s] = 0x80008000u;
 #pragma unroll
   for (int h = 0; h < 2; h++)
-    if (hw[h].known && hw[h].start == 0) init_half<C>(m, h, true, M);
+    if (hw[h].known && hw[h].start == 0) init_half<C>(ma, h, true, M);
 
+  static_assert(C::U == 2, "two register arrays alternate");
   const int ngroups = Lw / C::U;
+  LlrGroup<C> cur, nxt;
+  load_group<C>(hw, 0, cur);
   for (int g = 0; g < ngroups; g++) {
     const int i0 = g * C::U;
+    if (g + 1 < ngroups) load_group<C>(hw, i0 + C::U, nxt);  // prefetch the next group
     const bool masked = i0 < masked_until;
-    fwd_group<C, 0>(m, hw, i0, masked, M, sl);
-    if ((g % C::RN) == C::RN - 1) renorm<C>(m);
+    fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl);
+    fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl);
+    if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
+    cur = nxt;
   }
 
-  // traceback start (Alg. 2): after Lw stages (a multiple of K-1) slot = state
+  // traceback start (Alg. 2): best final metric, ties to the lowest state
   int s[2];
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     int best = 0;
-    uint32_t bv = (m[0] >> (16 * h)) & 0xffffu;
+    uint32_t bv = (ma[0] >> (16 * h)) & 0xffffu;
 #pragma unroll
     for (int q = 1; q < C::NS; q++) {
-      const uint32_t v = (m[q] >> (16 * h)) & 0xffffu;
+      const uint32_t v = (ma[q] >> (16 * h)) & 0xffffu;
       if (v > bv) {
         bv = v;
         best = q;
@@ -459,15 +467,306 @@ VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t 
       const int it = hw[h].start + (int)(hw[h].e0 - hw[h].t0);
       stop = it < stop ? it : stop;
     }
-  const int gstop = stop / C::U;
+  // blocks of TB stages, the next block's survivor words loaded ahead
+  constexpr int TB = 8;
   uint32_t acc[2] = {0u, 0u};
-  for (int g = ngroups - 1; g >= gstop; g--) {
-    const int i0 = g * C::U;
-    uint32_t w[C::KM1][C::WORDS];
+  uint32_t wc[TB][C::WORDS], wn[TB][C::WORDS];
+  int hi = Lw;  // exclusive upper iteration of the current block
+  int lo = hi - TB > stop ? hi - TB : stop;
+  lo = lo < 0 ? 0 : lo;
 #pragma unroll
-    for (int q = 0; q < C::KM1; q++) load_words<C>(sl, i0 + q, w[q]);
-    tb_group<C, 0>(i0, w, s, acc, hw);
+  for (int q = 0; q < TB; q++)
+    if (lo + q < hi) load_words<C>(sl, lo + q, wc[q]);
+  while (hi > stop) {
+    const int nhi = lo, nlo = (nhi - TB > stop) ? nhi - TB : stop;
+    if (nhi > stop) {
+#pragma unroll
+      for (int q = 0; q < TB; q++)
+        if (nlo + q < nhi) load_words<C>(sl, nlo + q, wn[q]);
+    }
+#pragma unroll
+    for (int q = TB - 1; q >= 0; q--)
+      if (lo + q < hi) tb_stage<C>(lo + q, wc[q], s, acc, hw);
+#pragma unroll
+    for (int q = 0; q < TB; q++)
+#pragma unroll
+      for (int k = 0; k < C::WORDS; k++) wc[q][k] = wn[q][k];
+    hi = nhi;
+    lo = nlo;
   }
 }
+
+
+#if defined(__CUDACC__)
+// ---------------------------------------------------------------------------
+// Several lanes per tile pair (K = 8, 9): G lanes hold NS = 64 slots each.
+// Slot s = (lane-in-group << NSB) | register.  Register s holds state
+// rotr(s, r) after r stages (rotation over K-1 bits), so each butterfly reads
+// and writes the two slots that differ in bit r mod (K-1): stages whose pair
+// bit is a register bit stay inside the lane, the others pair the same
+// register of two lanes (one shuffle each).  The part of a butterfly's branch
+// pattern that depends on the lane bits is applied by negating LLRs (Eq. 2 is
+// linear in the pattern bits), so every instruction is the same for all lanes.
+// ---------------------------------------------------------------------------
+
+// Branch-pattern offset (beta bits) contributed by the lane bits of the even
+// slot of phase P, for every phase, packed beta bits per phase.
+template <class C>
+__device__ __forceinline__ uint32_t lane_flip_mask(int lig) {
+  uint32_t mask = 0;
+#pragma unroll
+  for (int P = 0; P < C::KM1; P++) {
+    const int la = (P >= C::NSB) ? (lig & ~(1 << (P - C::NSB))) : lig;
+    const uint32_t R = rotr_w((uint32_t)la << C::NSB, P, C::KM1);
+    mask |= C::aout(R) << (C::BETA * P);
+  }
+  return mask;
+}
+
+template <class C, int P>
+__device__ __forceinline__ void rot_local_stage(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND],
+                                                uint32_t (&w)[C::WORDS]) {
+  constexpr int B = 1 << P;
+  constexpr int H = C::HALFP;
+#pragma unroll
+  for (int k = 0; k < C::WORDS; k++) w[k] = 0u;
+  uint32_t E[C::NS];
+#pragma unroll
+  for (int a = 0; a < C::NS; a++) {
+    if (a & B) continue;
+    const int b = a | B;
+    const uint32_t i0 = rotr_w((uint32_t)a, P, C::KM1);  // register part of the even predecessor
+    const uint32_t c00 = C::aout(i0), c01 = C::aout(i0 | 1u);
+    const uint32_t c10 = C::aout(i0 | (uint32_t)C::S), c11 = C::aout(i0 | (uint32_t)C::S | 1u);
+    const uint32_t x00 = add_bm<C>(m[a], D, c00), x01 = add_bm<C>(m[b], D, c01);
+    const uint32_t x10 = add_bm<C>(m[a], D, c10), x11 = add_bm<C>(m[b], D, c11);
+    E[a] = x00 - x01 + 0x8000u;
+    E[b] = x10 - x11 + 0x8000u;
+    m[a] = vmaxu2(x00, x01);
+    m[b] = vmaxu2(x10, x11);
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < C::NS; s2++) {
+    if (s2 & H) continue;
+    gather2<C>(w, s2, E[s2], E[s2 + H]);
+  }
+}
+
+// Pair bit P is lane bit P - NSB: the partner slot is the same register of
+// lane ^ (1 << (P - NSB)).  Both lanes form max(own + d, partner - d); the
+// decision polarity of the lane holding the odd slot is reversed (constant
+// cb), which the traceback undoes.
+template <class C, int P>
+__device__ __forceinline__ void rot_cross_stage(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND],
+                                                uint32_t (&w)[C::WORDS], int lig) {
+  constexpr int H = C::HALFP;
+  const int xm = 1 << (P - C::NSB);
+  const uint32_t cb = (lig & xm) ? 0xffff7fffu : 0x8000u;
+  constexpr uint32_t CM = (1u << C::BETA) - 1u;
+#pragma unroll
+  for (int k = 0; k < C::WORDS; k++) w[k] = 0u;
+  uint32_t E[C::NS];
+#pragma unroll
+  for (int r = 0; r < C::NS; r++) {
+    const uint32_t pv = __shfl_xor_sync(0xffffffffu, m[r], xm);
+    const uint32_t c = C::aout(rotr_w((uint32_t)r, P, C::KM1));
+    const uint32_t X = add_bm<C>(m[r], D, c);
+    const uint32_t Y = add_bm<C>(pv, D, (~c) & CM);
+    E[r] = X - Y + cb;
+    m[r] = vmaxu2(X, Y);
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < C::NS; s2++) {
+    if (s2 & H) continue;
+    gather2<C>(w, s2, E[s2], E[s2 + H]);
+  }
+}
+
+// Branch magnitudes of one stage with the lane's pattern offset for phase P.
+template <class C, int P>
+__device__ __forceinline__ void rot_stage_bm(int (&lA)[C::BETA], int (&lB)[C::BETA], uint32_t flip,
+                                             uint32_t (&D)[C::ND]) {
+#pragma unroll
+  for (int b = 0; b < C::BETA; b++) {
+    const int sgn = 1 - 2 * (int)((flip >> (C::BETA * P + b)) & 1u);
+    lA[b] *= sgn;
+    lB[b] *= sgn;
+  }
+  stage_bm<C>(lA, lB, D);
+}
+
+template <class C>
+__device__ __forceinline__ void load_stage(const Half (&hw)[2], int i, int (&l)[2][C::BETA]) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int64_t t = hw[h].t0 + (int64_t)((i > hw[h].start ? i : hw[h].start) - hw[h].start);
+    const int8_t* p = hw[h].llr + t * C::BETA;
+#pragma unroll
+    for (int b = 0; b < C::BETA; b++) l[h][b] = hw[h].active ? ld_s8(p + b) : 0;
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void rot_init_half(uint32_t (&m)[C::NS], int h, uint32_t M, int lig) {
+  const uint32_t keep = h ? 0x0000ffffu : 0xffff0000u;
+#pragma unroll
+  for (int r = 0; r < C::NS; r++) {
+    const uint32_t v = (lig == 0 && r == 0) ? 0x8000u : (0x8000u - M);
+    m[r] = (m[r] & keep) | (v << (16 * h));
+  }
+}
+
+template <class C, int P>
+__device__ __forceinline__ void rot_fwd_stage(uint32_t (&m)[C::NS], const Half (&hw)[2], int i, bool masked,
+                                              uint32_t M, int (&cur)[2][C::BETA], int (&nxt)[2][C::BETA],
+                                              bool more, uint32_t flip, int lig, Slab sl) {
+  if (more) load_stage<C>(hw, i + 1, nxt);  // prefetch the next stage
+  int lA[C::BETA], lB[C::BETA];
+#pragma unroll
+  for (int b = 0; b < C::BETA; b++) {
+    lA[b] = (!masked || i >= hw[0].start) ? cur[0][b] : 0;
+    lB[b] = (!masked || i >= hw[1].start) ? cur[1][b] : 0;
+  }
+  if (masked) {
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+      if (hw[h].known && i == hw[h].start) rot_init_half<C>(m, h, M, lig);
+  }
+  uint32_t D[C::ND];
+  rot_stage_bm<C, P>(lA, lB, flip, D);
+  uint32_t w[C::WORDS];
+  if constexpr (P < C::NSB)
+    rot_local_stage<C, P>(m, D, w);
+  else
+    rot_cross_stage<C, P>(m, D, w, lig);
+  store_words(sl.base + (int64_t)i * sl.stride, w, C::WORDS);
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+#pragma unroll
+    for (int b = 0; b < C::BETA; b++) cur[h][b] = nxt[h][b];
+}
+
+template <class C, int P>
+__device__ __forceinline__ void rot_fwd_group(uint32_t (&m)[C::NS], const Half (&hw)[2], int i0, bool masked,
+                                              uint32_t M, int (&cur)[2][C::BETA], int (&nxt)[2][C::BETA],
+                                              int Lw, uint32_t flip, int lig, Slab sl) {
+  if constexpr (P < C::KM1) {
+    rot_fwd_stage<C, P>(m, hw, i0 + P, masked, M, cur, nxt, i0 + P + 1 < Lw, flip, lig, sl);
+    rot_fwd_group<C, P + 1>(m, hw, i0, masked, M, cur, nxt, Lw, flip, lig, sl);
+  }
+}
+
+// Decodes the tile pair of a group of G lanes; lig = lane in group.  Lane
+// lig = h (h < 2) traces and emits tile h.
+template <class C>
+__device__ void decode_pair_rot(const Half (&hw)[2], int Lw, int masked_until, uint32_t M, Slab sl, int lane) {
+  const int lig = lane & (C::G - 1);
+  const int gbase = lane & ~(C::G - 1);
+  const uint32_t flip = lane_flip_mask<C>(lig);
+  uint32_t m[C::NS];
+#pragma unroll
+  for (int r = 0; r < C::NS; r++) m[r] = 0x80008000u;
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+    if (hw[h].known && hw[h].start == 0) rot_init_half<C>(m, h, M, lig);
+  const int ngroups = Lw / C::U;
+  int cur[2][C::BETA], nxt[2][C::BETA];
+  load_stage<C>(hw, 0, cur);
+  for (int g = 0; g < ngroups; g++) {
+    const int i0 = g * C::U;
+    rot_fwd_group<C, 0>(m, hw, i0, i0 < masked_until, M, cur, nxt, Lw, flip, lig, sl);
+    if ((g % C::RN) == C::RN - 1) {
+      const uint32_t ref = __shfl_sync(0xffffffffu, m[0], gbase);  // state 0 is slot 0 of the group
+#pragma unroll
+      for (int r = 0; r < C::NS; r++) m[r] = m[r] - ref + 0x80008000u;
+    }
+  }
+
+  // traceback start: best final metric of each tile over the group (slot =
+  // state after a multiple of K-1 stages), ties to the lowest state
+  int s[2];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    int best = 0;
+    uint32_t bv = (m[0] >> (16 * h)) & 0xffffu;
+#pragma unroll
+    for (int r = 1; r < C::NS; r++) {
+      const uint32_t v = (m[r] >> (16 * h)) & 0xffffu;
+      if (v > bv) {
+        bv = v;
+        best = r;
+      }
+    }
+    int bs = (lig << C::NSB) | best;
+#pragma unroll
+    for (int o = 1; o < C::G; o <<= 1) {
+      const uint32_t ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+      if (ov > bv || (ov == bv && os < bs)) {
+        bv = ov;
+        bs = os;
+      }
+    }
+    s[h] = hw[h].end_zero ? 0 : bs;
+  }
+  const int h = lig < 2 ? lig : 0;  // tile traced by this lane
+  const bool tracer = lig < 2 && hw[h].active;
+  int st = s[h];
+  int stop = Lw;
+  if (tracer && hw[h].e1 > hw[h].e0) stop = hw[h].start + (int)(hw[h].e0 - hw[h].t0);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int so = __shfl_xor_sync(0xffffffffu, stop, o);
+    stop = so < stop ? so : stop;
+  }
+  uint32_t acc = 0;
+  constexpr int TB = 8;
+  uint32_t wc[TB][C::WORDS], wn[TB][C::WORDS];
+  int hi = Lw;
+  int lo = hi - TB > stop ? hi - TB : stop;
+  lo = lo < 0 ? 0 : lo;
+#pragma unroll
+  for (int q = 0; q < TB; q++)
+    if (lo + q < hi) load_words<C>(sl, lo + q, wc[q]);
+  while (hi > stop) {
+    const int nhi = lo, nlo = (nhi - TB > stop) ? nhi - TB : stop;
+    if (nhi > stop) {
+#pragma unroll
+      for (int q = 0; q < TB; q++)
+        if (nlo + q < nhi) load_words<C>(sl, nlo + q, wn[q]);
+    }
+#pragma unroll
+    for (int q = TB - 1; q >= 0; q--) {
+      const int i = lo + q;
+      if (i >= hi) continue;
+      const int P = i % C::KM1;
+      const int src = gbase + (st >> C::NSB);
+      uint32_t ww[C::WORDS];
+#pragma unroll
+      for (int k = 0; k < C::WORDS; k++) ww[k] = __shfl_sync(0xffffffffu, wc[q][k], src);
+      const int r = st & (C::NS - 1);
+      const uint32_t word = pick_word<C>(ww, r);
+      const uint32_t pol = (h == 0 ? 1u : 0u) ^ ((P >= C::NSB && ((st >> P) & 1)) ? 1u : 0u);
+      const uint32_t d = ((word >> (16 * h + surv_pos<C>(r))) & 1u) ^ pol;
+      const uint32_t bit = (uint32_t)(st >> P) & 1u;
+      st = (st & ~(1 << P)) | (int)(d << P);
+      const int64_t t = hw[h].t0 + (int64_t)(i - hw[h].start);
+      if (tracer && t >= hw[h].e0 && t < hw[h].e1) {
+        acc |= bit << (t & 7);
+        if ((t & 7) == 0 || t == hw[h].e0) {
+          hw[h].out[t >> 3] = (uint8_t)acc;
+          acc = 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < TB; q++)
+#pragma unroll
+      for (int k = 0; k < C::WORDS; k++) wc[q][k] = wn[q][k];
+    hi = nhi;
+    lo = nlo;
+  }
+}
+#endif  // __CUDACC__
 
 }  // namespace vit

@@ -223,7 +223,8 @@ static size_t slab_task_words(const vit_code* c, int64_t n) {
 size_t vit_decode_workspace(const vit_code* c, int64_t n) {
   if (c == nullptr || n <= 0) return 0;
   const int64_t tiles = tile_count(n, c->f);
-  const int64_t tasks = (tiles + 63) / 64;
+  const int64_t tpt = c->entry->tiles_per_task;
+  const int64_t tasks = (tiles + tpt - 1) / tpt;
   size_t bytes = align_up((size_t)tasks * slab_task_words(c, n) * 4);
   if (c->period) bytes += align_up((size_t)n * c->beta);
   return bytes;
@@ -232,7 +233,8 @@ size_t vit_decode_workspace(const vit_code* c, int64_t n) {
 static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t* bits_out, void* ws,
                        size_t ws_bytes, cudaStream_t s) {
   const int64_t tiles = tile_count(n, c->f);
-  const int64_t tasks = (tiles + 63) / 64;
+  const int64_t tpt = c->entry->tiles_per_task;
+  const int64_t tasks = (tiles + tpt - 1) / tpt;
   const size_t tw = slab_task_words(c, n);
   uint8_t* p = (uint8_t*)ws;
   uint32_t* slab = (uint32_t*)p;
@@ -279,6 +281,19 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   return VIT_OK;
 }
+
+}  // extern "C"
+
+namespace vit {
+// Decode into a caller-supplied scratch area; shared by the public entry
+// points that bring their own device memory.
+int decode_into(const vit_code* c, const int8_t* llr, int64_t n, uint8_t* bits_out, void* ws, size_t ws_bytes,
+                cudaStream_t s) {
+  return decode_impl(c, llr, n, bits_out, ws, ws_bytes, s);
+}
+}  // namespace vit
+
+extern "C" {
 
 int vit_decode_ws(const vit_code* c, const int8_t* llr, int64_t n, uint8_t* bits_out, void* ws, size_t ws_bytes,
                   vit_stream_t stream) {
@@ -484,7 +499,7 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     }
     if (rc != VIT_OK) break;
     g.ntiles = tiles;
-    g.ntasks = (tiles + 63) / 64;
+    g.ntasks = (tiles + c->entry->tiles_per_task - 1) / c->entry->tiles_per_task;
     const int64_t U = c->entry->unroll;
     g.task_words = ((maxw + U - 1) / U * U) * 32 * c->entry->words;
     g.d_frames = (Frame*)dalloc(sizeof(Frame) * g.nframes);

@@ -43,10 +43,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) decode_tiles_kernel(cons
   const int lane = threadIdx.x & 31;
   const int64_t task = a.task_base + (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   if (task >= a.ntasks) return;  // warp-uniform
+  constexpr int TPT = 64 / C::G;  // tiles per task
+  const int pair = lane / C::G;
   Half hw[2];
 #pragma unroll
   for (int h = 0; h < 2; h++) {
-    const int64_t gt = task * 64 + 2 * lane + h;
+    const int64_t gt = task * TPT + 2 * pair + h;
     if (gt >= a.ntiles) {
       hw[h] = idle_half();
     } else if (a.frames == nullptr) {
@@ -73,7 +75,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) decode_tiles_kernel(cons
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
   Slab sl{a.slab + task * a.task_words + lane * C::WORDS, 32 * C::WORDS};
-  decode_pair<C>(hw, Lw, mu, a.M, sl);
+  if constexpr (C::G == 1)
+    decode_pair<C>(hw, Lw, mu, a.M, sl);
+  else
+    decode_pair_rot<C>(hw, Lw, mu, a.M, sl, lane);
 }
 #endif
 
@@ -83,6 +88,7 @@ struct CodeEntry {
   uint32_t polys[4];
   int words;  // survivor words per lane per stage
   int unroll; // stages per unrolled group
+  int tiles_per_task;
   cudaError_t (*launch)(const KArgs&, cudaStream_t);
 };
 
@@ -106,7 +112,7 @@ cudaError_t launch_decode(const KArgs& a, cudaStream_t s) {
 template <class C>
 constexpr CodeEntry make_entry() {
   return CodeEntry{C::K, C::BETA, {C::poly(0), C::poly(1), C::poly(2), C::poly(3)}, C::WORDS, C::U,
-                   &launch_decode<C>};
+                   64 / C::G, &launch_decode<C>};
 }
 #endif
 
@@ -130,4 +136,7 @@ struct vit_code {
 namespace vit {
 // Sets the thread-local message returned by vit_last_error and returns code.
 int set_error(int code, const char* fmt, ...);
+// Decodes one frame with the given device scratch (no argument checks).
+int decode_into(const vit_code* c, const int8_t* llr, int64_t n, uint8_t* bits_out, void* ws, size_t ws_bytes,
+                cudaStream_t s);
 }  // namespace vit

@@ -215,3 +215,44 @@ class Batch:
         if h is not None and _lib is not None:
             _lib.vit_batch_destroy(h)
             self._h = None
+
+
+def metric_workspace(code: Code, nframes: int, n: int, tau: float, C: int) -> int:
+    return int(load().vit_metric_workspace(code.handle, nframes, n, float(tau), C))
+
+
+class ViterbiMetric(torch.autograd.Function):
+    """Best-path metric of zero-terminated frames (tau == 0) or its
+    temperature-tau log-sum-exp relaxation (tau > 0), with a hand-written
+    backward (vit_metric_fwd / vit_metric_bwd).
+
+    llr: float32 CUDA tensor [F, n, beta]; returns float32 [F].
+    """
+
+    @staticmethod
+    def forward(ctx, llr: torch.Tensor, code: Code, tau: float = 0.0, C: int = 64):
+        if not (llr.is_cuda and llr.dtype == torch.float32 and llr.dim() == 3 and llr.shape[2] == code.beta):
+            raise ValueError("llr must be a float32 CUDA tensor [F, n, beta]")
+        x = llr.contiguous()
+        F, n, _ = x.shape
+        ws = torch.empty(max(metric_workspace(code, F, n, tau, C), 1), dtype=torch.uint8, device=x.device)
+        out = torch.empty(F, dtype=torch.float32, device=x.device)
+        _check(load().vit_metric_fwd(code.handle, x.data_ptr(), F, n, float(tau), C, out.data_ptr(),
+                                     ws.data_ptr(), ws.numel(), _stream(x.device)))
+        ctx.save_for_backward(x)
+        ctx.ws, ctx.code, ctx.tau, ctx.C = ws, code, float(tau), C
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        (x,) = ctx.saved_tensors
+        F, n, _ = x.shape
+        g = grad_out.contiguous().to(torch.float32)
+        grad = torch.empty_like(x)
+        _check(load().vit_metric_bwd(ctx.code.handle, x.data_ptr(), g.data_ptr(), F, n, ctx.tau, ctx.C,
+                                     ctx.ws.data_ptr(), ctx.ws.numel(), grad.data_ptr(), _stream(x.device)))
+        return grad, None, None, None
+
+
+def path_metric(llr: torch.Tensor, code: Code, tau: float = 0.0, C: int = 64) -> torch.Tensor:
+    return ViterbiMetric.apply(llr, code, tau, C)

@@ -64,7 +64,7 @@ def test_create_validates_arguments(lib):
     # invalid codes and tilings
     for args in ((2, 2, (3, 1), 0, 0), (10, 2, (1, 1), 0, 0), (7, 5, (1, 1, 1, 1, 1), 0, 0),
                  (7, 2, (0, 0o133), 0, 0), (7, 2, (0o400, 0o133), 0, 0), (9, 5, (1,) * 5, 0, 0),
-                 (7, 2, (0o171, 0o133), 1000, 48), (7, 2, (0o171, 0o133), -8, 0), (7, 2, (0o171, 0o133), 8, -1)):
+                 (7, 2, (0o171, 0o133), 1001, 48), (7, 2, (0o171, 0o133), -8, 0), (7, 2, (0o171, 0o133), 8, -1)):
         rc, h = _create(lib, *args)
         assert rc == -1 and not h.value, args
         assert lib.vit_last_error()

@@ -19,6 +19,7 @@ CODES = {
     "k3": (3, 2, (0o7, 0o5)),
     "k4b4": (4, 4, (0o13, 0o15, 0o17, 0o11)),
     "k6asym": (6, 2, (0o53, 0o46)),
+    "k9": synth.CODE_K9_R12,
 }
 
 
@@ -132,3 +133,34 @@ def test_config1_full_size_sampled(vit):
     # statistical sanity against the transmitted message: at 0 dB a rate-1/2
     # K=7 code is still above its waterfall (BER near 0.15)
     assert np.mean(got != s.bits) < 0.25
+
+
+def test_config4_k9_stream_sampled(vit):
+    # K=9 (561,753) stream, f=2048, v=96, Eb/N0 4 dB: tiles sampled against the oracle
+    K, beta, polys = CODES["k9"]
+    n = 1 << 22
+    s = synth.make_stream(_enc(CODES["k9"]), beta, n, 4.0, seed=4)
+    got = _gpu_decode(vit, CODES["k9"], s.llr, 2048, 96, oracle.STREAM, n)
+    ntiles = n // 2048
+    sample = np.unique(np.concatenate([[0, 1, ntiles - 1], synth.rng(8).integers(0, ntiles, 20)]))
+    for b in sample:
+        want = oracle.viterbi_blocked(K, beta, polys, s.llr, 2048, 96, 96, blocks=(int(b), int(b) + 1))
+        np.testing.assert_array_equal(got[b * 2048:(b + 1) * 2048], want[b * 2048:(b + 1) * 2048],
+                                      err_msg=f"tile {b}")
+    assert np.mean(got != s.bits) < 1e-3
+
+
+def test_config4_k7_punctured_sampled(vit):
+    # K=7 (171,133) punctured to rate 3/4 with [110;101], f=2048, v=64, 4 dB
+    K, beta, polys = CODES["k7"]
+    n = 1 << 22
+    mask = synth.PUNCT_R34
+    s = synth.make_stream(_enc(CODES["k7"]), beta, n, 4.0, seed=5, mask=mask)
+    got = _gpu_decode(vit, CODES["k7"], s.llr, 2048, 64, oracle.STREAM, n, puncture=mask)
+    dep = oracle.depuncture(s.llr, n, beta, mask)
+    ntiles = n // 2048
+    sample = np.unique(np.concatenate([[0, 1, ntiles - 1], synth.rng(9).integers(0, ntiles, 20)]))
+    for b in sample:
+        want = oracle.viterbi_blocked(K, beta, polys, dep, 2048, 64, 64, blocks=(int(b), int(b) + 1))
+        np.testing.assert_array_equal(got[b * 2048:(b + 1) * 2048], want[b * 2048:(b + 1) * 2048],
+                                      err_msg=f"tile {b}")
