@@ -118,6 +118,22 @@ int vit_decode_ws(const vit_code* code, const int8_t* llr, int64_t n, uint8_t* b
 int vit_decode(const vit_code* code, const int8_t* llr, int64_t n, uint8_t* bits_out, vit_stream_t stream);
 
 /*
+ * Allocation-free decode (the paper has no counterpart; this is a library
+ * service).  Same result as vit_decode_ws, for callers that cannot allocate
+ * device memory when they decode: real-time receive loops that must not call
+ * cudaMalloc, plugins handed only their input and output buffers, processes
+ * with a memory budget fixed at start-up.  The decoder scratch is a 16 MiB
+ * array compiled into the library (every GPU that loads it holds the array
+ * until exit); frames whose vit_decode_workspace(code, n) exceeds 16 MiB are
+ * rejected with VIT_EINVAL.  The first call on each device (with that device
+ * current) looks up the array's address, so make it before any stream
+ * capture.  All calls on a device share the array: calls whose work overlaps
+ * on the GPU (e.g. on different streams) race and must be serialised by the
+ * caller.  llr, n and bits_out are as for vit_decode_ws.
+ */
+int vit_decode_noalloc(const vit_code* code, const int8_t* llr, int64_t n, uint8_t* bits_out, vit_stream_t stream);
+
+/*
  * Convolutional encoder (Eq. 1) starting in state 0: bits is a device array
  * of n bytes (0/1, one input bit per stage); coded receives n*beta bytes
  * (0/1) stage-major.  Puncturing is not applied.
