@@ -73,59 +73,97 @@ def _traffic_per_launch():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region: NVML
+    (read-only queries through ctypes, every 2 ms), else nvidia-smi."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+    def __init__(self, cuda_index: int):
+        self.idx = cuda_index
+        self.samples = []  # (sm_mhz, max_mhz, reasons bitmask)
+        self._stop = threading.Event()
+        self._nvml = None
+        self._dev = None
+
+    def _open_nvml(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return False
+        if lib.nvmlInit_v2() != 0:
+            return False
+        dev = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.idx)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(dev)) == 0
+        except Exception:
+            ok = False
+        if not ok:
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.idx), ctypes.byref(dev)) == 0
+        if not ok:
+            return False
+        self._nvml, self._dev = lib, dev
+        return True
+
+    def _poll(self):
+        import ctypes
+        lib, dev = self._nvml, self._dev
+        fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(dev, 1, ctypes.byref(clk)) == 0 and \
+                    lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0:
+                r = rs.value if fn(dev, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((float(clk.value), float(mx.value), int(r)))
+            time.sleep(0.002)
+
+    def _smi(self):
+        fields = ("clocks.sm,clocks.max.sm,clocks_event_reasons.sw_power_cap,clocks_event_reasons.hw_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.hw_thermal_slowdown")
+        try:
+            proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={fields}",
+                                     "--format=csv,noheader,nounits", "-lms", "100"],
+                                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        bits = [0x4, 0x8, 0x20, 0x40]
+        for line in proc.stdout:
+            if self._stop.is_set():
+                break
+            parts = [x.strip() for x in line.split(",")]
+            try:
+                r = sum(b for b, v in zip(bits, parts[2:6]) if v.lower() == "active")
+                self.samples.append((float(parts[0]), float(parts[1]), r))
+            except (ValueError, IndexError):
+                continue
+        proc.terminate()
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self._t = threading.Thread(target=self._read, daemon=True)
-            self._t.start()
-        except OSError:
-            self.proc = None
+        target = self._poll if self._open_nvml() else self._smi
+        self._t = threading.Thread(target=target, daemon=True)
+        self._t.start()
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *a):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        self._stop.set()
+        self._t.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        sm = [x[0] for x in self.samples]
+        mask = 0
+        for x in self.samples:
+            mask |= x[2]
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": self.samples[-1][1],
+                "reasons": sorted(v for k, v in self.REASONS.items() if mask & k), "samples": len(sm),
+                "source": "nvml" if self._nvml is not None else "nvidia-smi"}
 
 
 def make_inputs(vit, code, device, torch, count=len(EBN0)):
@@ -219,6 +257,101 @@ def run_reference(args):
     }), flush=True)
 
 
+MIX_FRAMES = 4096
+MIX_WORKLOAD = ("4096 zero-terminated frames, info lengths U[40, 6144], half K=7 r1/3 (133,171,165), "
+                "half K=9 r1/2 (561,753), Eb/N0 U[1, 5] dB, int8 LLRs")
+
+
+def make_mixed_batch(vit, torch, device, nframes=MIX_FRAMES, seed=2):
+    """Frames of the mixed batch, encoded by the library (frames of one code are
+    encoded as one message: each K-1 zero tail returns the encoder to state 0)."""
+    from paper_2011_09337_gb300 import synth
+
+    spec = synth.mixed_batch_spec(nframes, seed)
+    codes = [synth.CODE_K7_R13, synth.CODE_K9_R12]
+    g = synth.rng(seed + 17)
+    frames = []  # (code index, llr device view, n, bits)
+    for ci, (K, beta, polys) in enumerate(codes):
+        idx = [i for i, fs in enumerate(spec) if fs.code == ci]
+        ns = [spec[i].n_info + K - 1 for i in idx]
+        msg = np.zeros(sum(ns), dtype=np.uint8)
+        sig = np.zeros(sum(ns) * beta)
+        off = 0
+        for i, n in zip(idx, ns):
+            msg[off:off + spec[i].n_info] = synth.info_bits(spec[i].n_info, g)
+            sig[off * beta:(off + n) * beta] = synth.noise_sigma(spec[i].ebn0_db, 1.0 / beta)
+            off += n
+        code = vit.Code(K, beta, polys)
+        coded = vit.encode(code, torch.from_numpy(msg).to(device)).cpu().numpy().reshape(-1)
+        y = (1.0 - 2.0 * coded) + sig * g.standard_normal(coded.size)
+        llr = torch.from_numpy(synth.quantize_llr(2.0 * y / (sig * sig))).to(device)
+        off = 0
+        for i, n in zip(idx, ns):
+            frames.append((ci, llr[off * beta:(off + n) * beta], n, msg[off:off + n]))
+            off += n
+    return codes, frames
+
+
+def mixed_batch_leg(vit, torch, device, steps):
+    from paper_2011_09337_gb300 import tune
+
+    codes, frames = make_mixed_batch(vit, torch, device)
+    info_bits = sum(n - (codes[ci][0] - 1) for ci, _, n, _ in frames)
+    tf = [(ci, llr, n, vit.TERMINATED) for ci, llr, n, _ in frames]
+    chosen, warps, report = tune.tune(tf, codes)
+    cobj = {ci: vit.Code(*codes[ci], f=chosen[ci].f, v=chosen[ci].v, mode=vit.TERMINATED) for ci in chosen}
+    sizes = [(cobj[ci].output_bits(n) + 7) // 8 for ci, _, n, _ in frames]
+    out = torch.zeros(sum(sizes), dtype=torch.uint8, device=device)
+    specs, views, off = [], [], 0
+    for (ci, llr, n, _), sz in zip(frames, sizes):
+        views.append(out[off:off + sz])
+        specs.append((cobj[ci], llr, n, vit.TERMINATED, views[-1]))
+        off += sz
+    batch = vit.Batch(specs, graph=True, warps=warps)
+    for _ in range(3):
+        batch.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        batch.run()
+    b.record()
+    torch.cuda.synchronize()
+    ms_batch = a.elapsed_time(b) / steps
+    # per-frame launches with the same tiling (one vit_decode_ws per frame)
+    ws = torch.empty(max(cobj[ci].workspace_bytes(n) for ci, _, n, _ in frames), dtype=torch.uint8, device=device)
+    pf_steps = max(1, min(steps, 3))
+    for ci, llr, n, _ in frames:
+        vit.decode(cobj[ci], llr, n, workspace=ws)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(pf_steps):
+        for (ci, llr, n, _), v in zip(frames, views):
+            vit.decode(cobj[ci], llr, n, out=v, workspace=ws)
+    b.record()
+    torch.cuda.synchronize()
+    ms_pf = a.elapsed_time(b) / pf_steps
+    # BER of the batched output against the transmitted bits
+    batch.run()
+    torch.cuda.synchronize()
+    host = out.cpu().numpy()
+    err, off = 0, 0
+    from paper_2011_09337_gb300 import synth
+    for (ci, _, n, bits), sz in zip(frames, sizes):
+        nb = n - (codes[ci][0] - 1)
+        err += int(np.sum(synth.unpack_bits(host[off:off + sz], nb) != bits[:nb]))
+        off += sz
+    return {
+        "workload": MIX_WORKLOAD, "value": info_bits / (ms_batch * 1e-3) / 1e6, "unit": "Mbit/s",
+        "ms_per_step": ms_batch, "per_frame": {"value": info_bits / (ms_pf * 1e-3) / 1e6, "unit": "Mbit/s",
+                                               "launches_per_step": len(frames), "ms_per_step": ms_pf},
+        "speedup_vs_per_frame": ms_pf / ms_batch, "launch": "one persistent two-code launch (CUDA graph)",
+        "tuned": {str(ci): {"f": chosen[ci].f, "v": chosen[ci].v, "disagree_vs_full_frame": chosen[ci].disagree}
+                  for ci in chosen} | {"warps_per_cta": warps},
+        "ber": err / info_bits, "info_bits": info_bits,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,6 +359,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-code batch leg")
     ap.add_argument("--profile", action="store_true",
                     help="build the workload with --streams streams, run the planned batch twice and exit "
                          "(the target of the ncu captures)")
@@ -338,6 +472,8 @@ def main():
     barrier()
     e2e_value = bits_per_step * world / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
 
+    mixed = None if args.no_mixed else mixed_batch_leg(vit, torch, dev, args.steps)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -367,6 +503,7 @@ def main():
                      "hbm_alg_gbs": alg_bytes / (launch_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_gbs},
         "clocks": clocks,
         "gpu_launches": args.steps,
+        "batch_mixed": mixed,
         "ber_6db": ber6,
     }
     if clocks.get("sm_mhz"):

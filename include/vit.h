@@ -157,6 +157,10 @@ typedef struct {
  * recorded: a plan decodes the same buffers every time it runs.  Tiling uses
  * each frame's code (f, v1, v2), or the autotuned tiling with VIT_BATCH_TUNE.
  */
+/* flags: VIT_BATCH_GRAPH captures the launch; bits 8..15 give the CTA size
+ * in warps (1..8, 0 = 4).  When the batch holds exactly two code groups for
+ * which a persistent two-code kernel is compiled, one launch pulls all their
+ * warp tasks from a queue ordered longest window first. */
 enum { VIT_BATCH_GRAPH = 1, VIT_BATCH_TUNE = 2 };
 int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int flags);
 int vit_batch_run(vit_batch* batch, vit_stream_t stream);

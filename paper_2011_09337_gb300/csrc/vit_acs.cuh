@@ -127,9 +127,21 @@ VIT_HD int ld_s8(const int8_t* p) {
 // ------------------------------------------------------- branch metrics
 // delta_c for coded pattern c (Eq. 2) from the ND magnitudes D[c'] (c' with
 // top bit 0): delta_{~c} = -delta_c.
+// m + k*d as one integer multiply-add: issued on the FMA pipe, which the
+// add-compare-select otherwise leaves idle (max, prmt and lop3 share the ALU).
+VIT_HD uint32_t madd(uint32_t d, uint32_t k, uint32_t m) {
+#if defined(__CUDA_ARCH__)
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(d), "r"(k), "r"(m));
+  return r;
+#else
+  return d * k + m;
+#endif
+}
+
 template <class C>
 VIT_HD uint32_t add_bm(uint32_t m, const uint32_t (&D)[C::ND], uint32_t c) {
-  return ((c >> (C::BETA - 1)) & 1u) ? m - D[(~c) & (C::ND - 1)] : m + D[c];
+  return ((c >> (C::BETA - 1)) & 1u) ? madd(D[(~c) & (C::ND - 1)], 0xffffffffu, m) : madd(D[c], 1u, m);
 }
 
 // Packs the stage's LLRs of both tiles (int8, sign-extended) as
@@ -524,31 +536,47 @@ __device__ __forceinline__ uint32_t lane_flip_mask(int lig) {
 }
 
 template <class C, int P>
+__device__ __forceinline__ void rot_butterfly(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND], int a, uint32_t& Ea,
+                                              uint32_t& Eb) {
+  const int b = a | (1 << P);
+  const uint32_t i0 = rotr_w((uint32_t)a, P, C::KM1);  // register part of the even predecessor
+  const uint32_t c00 = C::aout(i0), c01 = C::aout(i0 | 1u);
+  const uint32_t c10 = C::aout(i0 | (uint32_t)C::S), c11 = C::aout(i0 | (uint32_t)C::S | 1u);
+  const uint32_t x00 = add_bm<C>(m[a], D, c00), x01 = add_bm<C>(m[b], D, c01);
+  const uint32_t x10 = add_bm<C>(m[a], D, c10), x11 = add_bm<C>(m[b], D, c11);
+  Ea = x00 - x01 + 0x8000u;
+  Eb = x10 - x11 + 0x8000u;
+  m[a] = vmaxu2(x00, x01);
+  m[b] = vmaxu2(x10, x11);
+}
+
+// Pair bit P is a register bit: butterflies inside the lane, visited so that
+// each prmt pair (s, s + HALFP) is finished together.
+template <class C, int P>
 __device__ __forceinline__ void rot_local_stage(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND],
                                                 uint32_t (&w)[C::WORDS]) {
   constexpr int B = 1 << P;
   constexpr int H = C::HALFP;
 #pragma unroll
   for (int k = 0; k < C::WORDS; k++) w[k] = 0u;
-  uint32_t E[C::NS];
+  if constexpr (B == H) {
 #pragma unroll
-  for (int a = 0; a < C::NS; a++) {
-    if (a & B) continue;
-    const int b = a | B;
-    const uint32_t i0 = rotr_w((uint32_t)a, P, C::KM1);  // register part of the even predecessor
-    const uint32_t c00 = C::aout(i0), c01 = C::aout(i0 | 1u);
-    const uint32_t c10 = C::aout(i0 | (uint32_t)C::S), c11 = C::aout(i0 | (uint32_t)C::S | 1u);
-    const uint32_t x00 = add_bm<C>(m[a], D, c00), x01 = add_bm<C>(m[b], D, c01);
-    const uint32_t x10 = add_bm<C>(m[a], D, c10), x11 = add_bm<C>(m[b], D, c11);
-    E[a] = x00 - x01 + 0x8000u;
-    E[b] = x10 - x11 + 0x8000u;
-    m[a] = vmaxu2(x00, x01);
-    m[b] = vmaxu2(x10, x11);
-  }
+    for (int a = 0; a < C::NS; a++) {
+      if (a & B) continue;
+      uint32_t Ea, Eb;
+      rot_butterfly<C, P>(m, D, a, Ea, Eb);
+      gather2<C>(w, a, Ea, Eb);
+    }
+  } else {
 #pragma unroll
-  for (int s2 = 0; s2 < C::NS; s2++) {
-    if (s2 & H) continue;
-    gather2<C>(w, s2, E[s2], E[s2 + H]);
+    for (int a = 0; a < C::NS; a++) {
+      if ((a & B) || (a & H)) continue;
+      uint32_t E0, E1, E2, E3;  // slots a, a|B, a+H, (a+H)|B
+      rot_butterfly<C, P>(m, D, a, E0, E1);
+      rot_butterfly<C, P>(m, D, a | H, E2, E3);
+      gather2<C>(w, a, E0, E2);
+      gather2<C>(w, a | B, E1, E3);
+    }
   }
 }
 
@@ -565,20 +593,21 @@ __device__ __forceinline__ void rot_cross_stage(uint32_t (&m)[C::NS], const uint
   constexpr uint32_t CM = (1u << C::BETA) - 1u;
 #pragma unroll
   for (int k = 0; k < C::WORDS; k++) w[k] = 0u;
-  uint32_t E[C::NS];
 #pragma unroll
-  for (int r = 0; r < C::NS; r++) {
-    const uint32_t pv = __shfl_xor_sync(0xffffffffu, m[r], xm);
-    const uint32_t c = C::aout(rotr_w((uint32_t)r, P, C::KM1));
-    const uint32_t X = add_bm<C>(m[r], D, c);
-    const uint32_t Y = add_bm<C>(pv, D, (~c) & CM);
-    E[r] = X - Y + cb;
-    m[r] = vmaxu2(X, Y);
-  }
+  for (int r0 = 0; r0 < C::NS; r0++) {
+    if (r0 & H) continue;
+    uint32_t E[2];
 #pragma unroll
-  for (int s2 = 0; s2 < C::NS; s2++) {
-    if (s2 & H) continue;
-    gather2<C>(w, s2, E[s2], E[s2 + H]);
+    for (int q = 0; q < 2; q++) {
+      const int r = r0 + q * H;
+      const uint32_t pv = __shfl_xor_sync(0xffffffffu, m[r], xm);
+      const uint32_t c = C::aout(rotr_w((uint32_t)r, P, C::KM1));
+      const uint32_t X = add_bm<C>(m[r], D, c);
+      const uint32_t Y = add_bm<C>(pv, D, (~c) & CM);
+      E[q] = X - Y + cb;
+      m[r] = vmaxu2(X, Y);
+    }
+    gather2<C>(w, r0, E[0], E[1]);
   }
 }
 
@@ -710,10 +739,17 @@ __device__ void decode_pair_rot(const Half (&hw)[2], int Lw, int masked_until, u
     s[h] = hw[h].end_zero ? 0 : bs;
   }
   const int h = lig < 2 ? lig : 0;  // tile traced by this lane
-  const bool tracer = lig < 2 && hw[h].active;
-  int st = s[h];
+  // fields of the traced tile, selected without indexing hw at run time
+  const bool sel1 = (h == 1);
+  const int64_t tt0 = sel1 ? hw[1].t0 : hw[0].t0;
+  const int64_t te0 = sel1 ? hw[1].e0 : hw[0].e0;
+  const int64_t te1 = sel1 ? hw[1].e1 : hw[0].e1;
+  const int tstart = sel1 ? hw[1].start : hw[0].start;
+  uint8_t* tout = sel1 ? hw[1].out : hw[0].out;
+  const bool tracer = lig < 2 && (sel1 ? hw[1].active : hw[0].active);
+  int st = sel1 ? s[1] : s[0];
   int stop = Lw;
-  if (tracer && hw[h].e1 > hw[h].e0) stop = hw[h].start + (int)(hw[h].e0 - hw[h].t0);
+  if (tracer && te1 > te0) stop = tstart + (int)(te0 - tt0);
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int so = __shfl_xor_sync(0xffffffffu, stop, o);
@@ -750,11 +786,11 @@ __device__ void decode_pair_rot(const Half (&hw)[2], int Lw, int masked_until, u
       const uint32_t d = ((word >> (16 * h + surv_pos<C>(r))) & 1u) ^ pol;
       const uint32_t bit = (uint32_t)(st >> P) & 1u;
       st = (st & ~(1 << P)) | (int)(d << P);
-      const int64_t t = hw[h].t0 + (int64_t)(i - hw[h].start);
-      if (tracer && t >= hw[h].e0 && t < hw[h].e1) {
+      const int64_t t = tt0 + (int64_t)(i - tstart);
+      if (tracer && t >= te0 && t < te1) {
         acc |= bit << (t & 7);
-        if ((t & 7) == 0 || t == hw[h].e0) {
-          hw[h].out[t >> 3] = (uint8_t)acc;
+        if ((t & 7) == 0 || t == te0) {
+          tout[t >> 3] = (uint8_t)acc;
           acc = 0;
         }
       }

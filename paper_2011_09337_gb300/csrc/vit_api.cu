@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <string>
@@ -122,6 +123,49 @@ void register_codes(const CodeEntry* e, int n) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   for (int i = 0; i < n; i++) registry().push_back(e[i]);
 }
+namespace mixreg {
+struct MixReg {
+  MixKey a, b;
+  cudaError_t (*launch)(const MixArgs&, int, cudaStream_t);
+  MixEntry entry;
+};
+std::vector<MixReg>& mix_registry() {
+  static std::vector<MixReg> r;
+  return r;
+}
+bool key_matches(const MixKey& k, const CodeEntry* e) {
+  if (e == nullptr || k.K != e->K || k.beta != e->beta) return false;
+  for (int b = 0; b < k.beta; b++)
+    if (k.polys[b] != e->polys[b]) return false;
+  return true;
+}
+}  // namespace mixreg
+using namespace mixreg;
+
+void register_mixed(const MixKey& a, const MixKey& b, cudaError_t (*launch)(const MixArgs&, int, cudaStream_t)) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  mix_registry().push_back(MixReg{a, b, launch, MixEntry{{nullptr, nullptr}, launch}});
+}
+
+const MixEntry* find_mixed(const CodeEntry* x, const CodeEntry* y, bool* swapped) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (MixReg& r : mix_registry()) {
+    if (key_matches(r.a, x) && key_matches(r.b, y)) {
+      *swapped = false;
+      r.entry.code[0] = x;
+      r.entry.code[1] = y;
+      return &r.entry;
+    }
+    if (key_matches(r.a, y) && key_matches(r.b, x)) {
+      *swapped = true;
+      r.entry.code[0] = y;
+      r.entry.code[1] = x;
+      return &r.entry;
+    }
+  }
+  return nullptr;
+}
+
 const CodeEntry* find_code(int K, int beta, const uint32_t* polys) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   for (const CodeEntry& e : registry()) {
@@ -277,7 +321,7 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
   a.slab = slab;
   a.task_words = (int64_t)tw;
   a.task_base = 0;
-  cudaError_t e = c->entry->launch(a, s);
+  cudaError_t e = c->entry->launch(a, kWarpsPerCta, s);
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   return VIT_OK;
 }
@@ -353,6 +397,7 @@ struct vit_batch {
     Frame* d_frames = nullptr;
     int64_t* d_tile0 = nullptr;
     uint32_t* d_slab = nullptr;
+    std::vector<int64_t> task_len;  // host estimate of each task's window length
   };
   struct Dep {
     const int8_t* src;
@@ -364,9 +409,14 @@ struct vit_batch {
   std::vector<Dep> deps;
   std::vector<void*> allocs;
   int flags = 0;
+  int warps = kWarpsPerCta;
+  const MixEntry* mix = nullptr;  // persistent two-code kernel, when available
+  int mix_group[2] = {0, 1};
+  MixTask* d_queue = nullptr;
+  int64_t nqueue = 0;
+  unsigned long long* d_counter = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int launches = 0;
 };
 
 namespace {
@@ -394,6 +444,21 @@ void batch_free(vit_batch* b) {
   delete b;
 }
 
+KArgs group_args(const vit_batch::Group& g) {
+  KArgs a;
+  memset(&a, 0, sizeof a);
+  a.frames = g.d_frames;
+  a.tile0 = g.d_tile0;
+  a.nframes = g.nframes;
+  a.ntiles = g.ntiles;
+  a.tl = g.tl;
+  a.M = g.M;
+  a.ntasks = g.ntasks;
+  a.slab = g.d_slab;
+  a.task_words = g.task_words;
+  return a;
+}
+
 int batch_enqueue(vit_batch* b, cudaStream_t s) {
   for (const auto& d : b->deps) {
     const unsigned grid = (unsigned)((d.n + 255) / 256);
@@ -401,19 +466,22 @@ int batch_enqueue(vit_batch* b, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "depuncture launch");
   }
+  if (b->mix) {
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    MixArgs m;
+    memset(&m, 0, sizeof m);
+    m.g[0] = group_args(b->groups[b->mix_group[0]]);
+    m.g[1] = group_args(b->groups[b->mix_group[1]]);
+    m.queue = b->d_queue;
+    m.nqueue = b->nqueue;
+    m.counter = b->d_counter;
+    e = b->mix->launch(m, b->warps, s);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent decode launch");
+    return VIT_OK;
+  }
   for (const auto& g : b->groups) {
-    KArgs a;
-    memset(&a, 0, sizeof a);
-    a.frames = g.d_frames;
-    a.tile0 = g.d_tile0;
-    a.nframes = g.nframes;
-    a.ntiles = g.ntiles;
-    a.tl = g.tl;
-    a.M = g.M;
-    a.ntasks = g.ntasks;
-    a.slab = g.d_slab;
-    a.task_words = g.task_words;
-    cudaError_t e = g.entry->launch(a, s);
+    cudaError_t e = g.entry->launch(group_args(g), b->warps, s);
     if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");
   }
   return VIT_OK;
@@ -435,12 +503,14 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     if (f.mode == VIT_TERMINATED && f.n <= f.code->K - 1)
       return fail(VIT_EINVAL, "frame %d: terminated frame shorter than its tail", i);
   }
+  const int warps = (flags >> 8) & 0xff;
+  if (warps != 0 && (warps < 1 || warps > 8)) return fail(VIT_EINVAL, "warps per CTA must be in [1, 8]");
   vit_batch* b = new (std::nothrow) vit_batch;
   if (b == nullptr) return fail(VIT_ENOMEM, "out of host memory");
   b->flags = flags;
-  // group frames by (kernel, tiling), keeping frame order inside a group
-  std::vector<int> order(nframes);
-  for (int i = 0; i < nframes; i++) order[i] = i;
+  b->warps = warps ? warps : kWarpsPerCta;
+  // group frames by (kernel, tiling); inside a group, longest frames first so
+  // that the tiles of one warp task have similar windows
   std::vector<std::vector<int>> members;
   std::vector<const vit_code*> leaders;
   for (int i = 0; i < nframes; i++) {
@@ -457,6 +527,8 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     }
     members[gi].push_back(i);
   }
+  for (auto& m : members)
+    std::stable_sort(m.begin(), m.end(), [&](int x, int y) { return frames[x].n > frames[y].n; });
   int rc = VIT_OK;
   auto dalloc = [&](size_t bytes) -> void* {
     void* p = nullptr;
@@ -473,6 +545,7 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     g.nframes = (int)members[k].size();
     std::vector<Frame> hf(g.nframes);
     std::vector<int64_t> ht0(g.nframes);
+    std::vector<int64_t> tile_len_host;  // window length of every tile, in order
     int64_t tiles = 0, maxw = 1;
     for (int j = 0; j < g.nframes; j++) {
       const vit_frame& f = frames[members[k][j]];
@@ -493,13 +566,24 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
       hf[j].n_out = (f.mode == VIT_TERMINATED) ? f.n - (fc->K - 1) : f.n;
       hf[j].mode = f.mode;
       ht0[j] = tiles;
-      tiles += tile_count(f.n, c->f);
+      const int64_t nt = tile_count(f.n, c->f);
+      for (int64_t t = 0; t < nt; t++) {
+        const Half h = make_half(hf[j], t, g.tl);
+        tile_len_host.push_back(h.t1 - h.t0);
+      }
+      tiles += nt;
       const int64_t w = max_window(c, f.n);
       if (w > maxw) maxw = w;
     }
     if (rc != VIT_OK) break;
     g.ntiles = tiles;
-    g.ntasks = (tiles + c->entry->tiles_per_task - 1) / c->entry->tiles_per_task;
+    const int64_t tpt = c->entry->tiles_per_task;
+    g.ntasks = (tiles + tpt - 1) / tpt;
+    g.task_len.assign((size_t)g.ntasks, 0);
+    for (int64_t t = 0; t < tiles; t++) {
+      int64_t& L = g.task_len[(size_t)(t / tpt)];
+      L = tile_len_host[(size_t)t] > L ? tile_len_host[(size_t)t] : L;
+    }
     const int64_t U = c->entry->unroll;
     g.task_words = ((maxw + U - 1) / U * U) * 32 * c->entry->words;
     g.d_frames = (Frame*)dalloc(sizeof(Frame) * g.nframes);
@@ -515,7 +599,41 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
       rc = cuda_fail(e, "plan upload");
       break;
     }
-    b->groups.push_back(g);
+    b->groups.push_back(std::move(g));
+  }
+  // two code groups with a compiled persistent kernel: one launch over a
+  // queue of all their tasks, longest windows first
+  if (rc == VIT_OK && b->groups.size() == 2) {
+    bool swapped = false;
+    const MixEntry* mx = find_mixed(b->groups[0].entry, b->groups[1].entry, &swapped);
+    if (mx != nullptr) {
+      b->mix = mx;
+      b->mix_group[0] = swapped ? 1 : 0;
+      b->mix_group[1] = swapped ? 0 : 1;
+      std::vector<MixTask> q;
+      std::vector<int64_t> cost;
+      for (int slot = 0; slot < 2; slot++) {
+        const auto& g = b->groups[b->mix_group[slot]];
+        for (int64_t t = 0; t < g.ntasks; t++) {
+          q.push_back(MixTask{slot, 0, t});
+          cost.push_back(g.task_len[(size_t)t]);
+        }
+      }
+      std::vector<size_t> ord(q.size());
+      for (size_t i = 0; i < ord.size(); i++) ord[i] = i;
+      std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+      std::vector<MixTask> qs(q.size());
+      for (size_t i = 0; i < ord.size(); i++) qs[i] = q[ord[i]];
+      b->nqueue = (int64_t)qs.size();
+      b->d_queue = (MixTask*)dalloc(sizeof(MixTask) * qs.size());
+      b->d_counter = (unsigned long long*)dalloc(sizeof(unsigned long long));
+      if (!b->d_queue || !b->d_counter) {
+        rc = fail(VIT_ENOMEM, "device allocation failed");
+      } else {
+        cudaError_t e = cudaMemcpy(b->d_queue, qs.data(), sizeof(MixTask) * qs.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_fail(e, "queue upload");
+      }
+    }
   }
   if (rc != VIT_OK) {
     batch_free(b);

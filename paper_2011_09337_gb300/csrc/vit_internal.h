@@ -8,7 +8,8 @@
 
 namespace vit {
 
-constexpr int kWarpsPerCta = 4;
+constexpr int kWarpsPerCta = 4;   // default CTA size (warps)
+constexpr int kMaxRegs = 168;     // registers per thread of the tile decoders
 
 // Arguments of the tile decoder.  A "task" is one warp: 32 lanes x 2 tiles.
 struct KArgs {
@@ -38,11 +39,10 @@ VIT_HD int64_t find_frame(const int64_t* tile0, int nframes, int64_t gt) {
 }
 
 #if defined(__CUDACC__)
+// Decodes warp task `task` of one code: 64 / G tiles, lanes grouped G per
+// tile pair.
 template <class C>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 3) decode_tiles_kernel(const KArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t task = a.task_base + (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
-  if (task >= a.ntasks) return;  // warp-uniform
+__device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane) {
   constexpr int TPT = 64 / C::G;  // tiles per task
   const int pair = lane / C::G;
   Half hw[2];
@@ -80,6 +80,51 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) decode_tiles_kernel(cons
   else
     decode_pair_rot<C>(hw, Lw, mu, a.M, sl, lane);
 }
+
+// One warp per task, tasks in launch order.
+template <class C>
+__global__ void __maxnreg__(kMaxRegs) decode_tiles_kernel(const KArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t task = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (task >= a.ntasks) return;  // warp-uniform
+  run_task<C>(a, task, lane);
+}
+
+// Persistent kernel over the tasks of two codes: each warp takes the next
+// entry of a cost-ordered queue (one atomic per task) until it is empty.
+struct MixTask {
+  int32_t code;  // 0 or 1
+  int32_t pad;
+  int64_t task;  // task index within that code's launch arguments
+};
+struct MixArgs {
+  KArgs g[2];
+  const MixTask* queue;
+  int64_t nqueue;
+  unsigned long long* counter;  // zeroed before every launch
+};
+
+// Out-of-line task bodies keep the two codes' register allocations apart.
+template <class C>
+__device__ __noinline__ void run_task_call(const KArgs a, int64_t task, int lane) {
+  run_task<C>(a, task, lane);
+}
+
+template <class C0, class C1>
+__global__ void __maxnreg__(kMaxRegs) decode_mixed_kernel(const MixArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long q = 0;
+    if (lane == 0) q = atomicAdd(a.counter, 1ull);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= (unsigned long long)a.nqueue) break;
+    const MixTask t = a.queue[q];
+    if (t.code == 0)
+      run_task_call<C0>(a.g[0], t.task, lane);
+    else
+      run_task_call<C1>(a.g[1], t.task, lane);
+  }
+}
 #endif
 
 // One compiled code.
@@ -89,24 +134,48 @@ struct CodeEntry {
   int words;  // survivor words per lane per stage
   int unroll; // stages per unrolled group
   int tiles_per_task;
-  cudaError_t (*launch)(const KArgs&, cudaStream_t);
+  cudaError_t (*launch)(const KArgs&, int warps, cudaStream_t);
+};
+
+// A compiled persistent kernel for a pair of codes.
+struct MixEntry {
+  const CodeEntry* code[2];
+  cudaError_t (*launch)(const MixArgs&, int warps, cudaStream_t);
 };
 
 #if defined(__CUDACC__)
 template <class C>
-cudaError_t launch_decode(const KArgs& a, cudaStream_t s) {
+cudaError_t launch_decode(const KArgs& a, int warps, cudaStream_t s) {
+  if (warps < 1 || warps > 8) warps = kWarpsPerCta;
   // grid.x is limited to 2^31-1 CTAs; split very large launches
   const int64_t maxc = (int64_t)1 << 30;
-  for (int64_t t0 = 0; t0 < a.ntasks; t0 += maxc * kWarpsPerCta) {
+  for (int64_t t0 = 0; t0 < a.ntasks; t0 += maxc * warps) {
     KArgs b = a;
     b.task_base = t0;
-    const int64_t tasks = (a.ntasks - t0 < maxc * kWarpsPerCta) ? a.ntasks - t0 : maxc * kWarpsPerCta;
-    const unsigned grid = (unsigned)((tasks + kWarpsPerCta - 1) / kWarpsPerCta);
-    decode_tiles_kernel<C><<<grid, kWarpsPerCta * 32, 0, s>>>(b);
+    const int64_t tasks = (a.ntasks - t0 < maxc * warps) ? a.ntasks - t0 : maxc * warps;
+    const unsigned grid = (unsigned)((tasks + warps - 1) / warps);
+    decode_tiles_kernel<C><<<grid, warps * 32, 0, s>>>(b);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+template <class C0, class C1>
+cudaError_t launch_mixed(const MixArgs& a, int warps, cudaStream_t s) {
+  if (warps < 1 || warps > 8) warps = kWarpsPerCta;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_mixed_kernel<C0, C1>, warps * 32, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)sms * per_sm;
+  const int64_t need = (a.nqueue + warps - 1) / warps;
+  if (grid > need) grid = need > 0 ? need : 1;
+  decode_mixed_kernel<C0, C1><<<(unsigned)grid, warps * 32, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <class C>
@@ -119,6 +188,14 @@ constexpr CodeEntry make_entry() {
 // Registry filled by the per-code translation units.
 const CodeEntry* find_code(int K, int beta, const uint32_t* polys);
 void register_codes(const CodeEntry* e, int n);
+// Persistent two-code kernels, registered by their translation units with
+// the codes' (K, beta, polys); looked up by code entry.
+struct MixKey {
+  int K, beta;
+  uint32_t polys[4];
+};
+void register_mixed(const MixKey& a, const MixKey& b, cudaError_t (*launch)(const MixArgs&, int, cudaStream_t));
+const MixEntry* find_mixed(const CodeEntry* a, const CodeEntry* b, bool* swapped);
 
 }  // namespace vit
 

@@ -187,8 +187,9 @@ class Batch:
     buffers every time ``run()`` is called; ``graph=True`` replays one
     captured CUDA graph."""
 
-    def __init__(self, frames, graph: bool = True):
-        """frames: iterable of (code, llr, n, mode, out) with CUDA tensors."""
+    def __init__(self, frames, graph: bool = True, warps: int = 0):
+        """frames: iterable of (code, llr, n, mode, out) with CUDA tensors;
+        warps: CTA size in warps (1..8, 0 = library default)."""
         L = load()
         self._keep = []
         arr = (_Frame * len(frames))()
@@ -203,7 +204,8 @@ class Batch:
             arr[i] = _Frame(code.handle.value, llr.data_ptr(), n, mode, out.data_ptr())
             self._keep.append((code, llr, out))
         h = ctypes.c_void_p()
-        _check(L.vit_batch_plan(ctypes.byref(h), arr, len(frames), BATCH_GRAPH if graph else 0))
+        flags = (BATCH_GRAPH if graph else 0) | ((int(warps) & 0xFF) << 8)
+        _check(L.vit_batch_plan(ctypes.byref(h), arr, len(frames), flags))
         self._h = h
         self.device = frames[0][1].device
 

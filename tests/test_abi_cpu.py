@@ -83,10 +83,10 @@ def test_counts_and_workspace(lib):
     assert lib.vit_set_termination(h, 1) == 0
     assert lib.vit_output_bits(h, 1000) == 994
     assert lib.vit_set_termination(h, 7) == -1
-    # workspace: ceil(tiles / 64) tasks x (window rounded to 6) x 32 lanes x 16 bytes
+    # workspace: ceil(tiles / 64) tasks x (window rounded to 2) x 32 lanes x 16 bytes
     n = 1 << 20
     tiles = n // 1024
-    want = ((tiles + 63) // 64) * 1122 * 32 * 16
+    want = ((tiles + 63) // 64) * 1120 * 32 * 16
     assert lib.vit_decode_workspace(h, n) == (want + 255) // 256 * 256
     # rate-3/4 puncturing [110;101]: 4 symbols per 3 stages
     mask = (ctypes.c_uint8 * 6)(1, 1, 0, 1, 0, 1)
