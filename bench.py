@@ -226,14 +226,18 @@ def run_reference(args):
     from paper_2011_09337_gb300 import synth
 
     cores = len(os.sched_getaffinity(0))
-    n = 64 * F
+    n = 1024 * F
     s = synth.make_stream(lambda x: oracle.encode(K, BETA, POLYS, x), BETA, n, 3.0, seed=7)
-    tiles_per_step = cores * 2
+    tiles_per_step = cores * 64
+    state = {"next": 1}
 
     def step():
-        chunks = np.array_split(np.arange(tiles_per_step) % 62 + 1, cores)
+        # consecutive tiles of the sample stream, split evenly over the host cores
+        first = state["next"]
+        state["next"] = first + tiles_per_step if first + 2 * tiles_per_step < 1023 else 1
+        chunks = np.array_split(np.arange(first, first + tiles_per_step), cores)
         ths = [threading.Thread(target=oracle.viterbi_blocked, args=(K, BETA, POLYS, s.llr, F, V, V),
-                                kwargs={"blocks": (int(c[0]), int(c[0]) + len(c))}) for c in chunks if len(c)]
+                                kwargs={"blocks": (int(c[0]), int(c[-1]) + 1)}) for c in chunks if len(c)]
         for t in ths:
             t.start()
         for t in ths:

@@ -25,6 +25,7 @@
 // word wd(j) is the (A-inverted) decision of state j, tile h.
 #pragma once
 #include <stdint.h>
+#include <string.h>
 
 #if defined(__CUDACC__)
 #define VIT_HD __host__ __device__ __forceinline__
@@ -127,21 +128,9 @@ VIT_HD int ld_s8(const int8_t* p) {
 // ------------------------------------------------------- branch metrics
 // delta_c for coded pattern c (Eq. 2) from the ND magnitudes D[c'] (c' with
 // top bit 0): delta_{~c} = -delta_c.
-// m + k*d as one integer multiply-add: issued on the FMA pipe, which the
-// add-compare-select otherwise leaves idle (max, prmt and lop3 share the ALU).
-VIT_HD uint32_t madd(uint32_t d, uint32_t k, uint32_t m) {
-#if defined(__CUDA_ARCH__)
-  uint32_t r;
-  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(d), "r"(k), "r"(m));
-  return r;
-#else
-  return d * k + m;
-#endif
-}
-
 template <class C>
 VIT_HD uint32_t add_bm(uint32_t m, const uint32_t (&D)[C::ND], uint32_t c) {
-  return ((c >> (C::BETA - 1)) & 1u) ? madd(D[(~c) & (C::ND - 1)], 0xffffffffu, m) : madd(D[c], 1u, m);
+  return ((c >> (C::BETA - 1)) & 1u) ? m - D[(~c) & (C::ND - 1)] : m + D[c];
 }
 
 // Packs the stage's LLRs of both tiles (int8, sign-extended) as
@@ -346,6 +335,82 @@ VIT_HD void load_group(const Half (&hw)[2], int i, LlrGroup<C>& g) {
     }
 }
 
+// Same loads once every window of the warp has started: stage t of tile h is
+// at llr + (t0 - start + i) * beta, one base address per group.
+template <class C>
+VIT_HD void load_group_fast(const Half (&hw)[2], int i, LlrGroup<C>& g) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int8_t* p = hw[h].llr + (hw[h].t0 - hw[h].start + (int64_t)i) * C::BETA;
+#pragma unroll
+    for (int u = 0; u < C::U; u++)
+#pragma unroll
+      for (int b = 0; b < C::BETA; b++) g.v[u][h][b] = hw[h].active ? ld_s8(p + u * C::BETA + b) : 0;
+  }
+}
+
+// Word loads: when every tile's group of U stages starts on a 4-byte boundary
+// (U*beta a multiple of 4), one 32-bit load per tile fetches the group's
+// LLRs, and prmt spreads them; 4x fewer load instructions and L1 wavefronts
+// than byte loads.
+template <class C>
+constexpr bool kWordLoads = (C::U * C::BETA) % 4 == 0;
+
+template <class C>
+VIT_HD uint32_t ld_u32(const int8_t* p) {
+#if defined(__CUDA_ARCH__)
+  return __ldg(reinterpret_cast<const unsigned int*>(p));
+#else
+  uint32_t v;
+  memcpy(&v, p, 4);
+  return v;
+#endif
+}
+
+template <class C>
+VIT_HD void load_group_words(const Half (&hw)[2], int i, uint32_t (&w)[2][C::U * C::BETA / 4]) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int8_t* p = hw[h].llr + (hw[h].t0 - hw[h].start + (int64_t)i) * C::BETA;
+#pragma unroll
+    for (int k = 0; k < C::U * C::BETA / 4; k++) w[h][k] = hw[h].active ? ld_u32<C>(p + 4 * k) : 0u;
+  }
+}
+
+// Sign-extended byte q of the group's words of tile h.
+template <class C>
+VIT_HD int word_byte(const uint32_t (&w)[2][C::U * C::BETA / 4], int h, int q) {
+  return (int)(int8_t)((w[h][q >> 2] >> (8 * (q & 3))) & 0xffu);
+}
+
+// Integer-encoded LLR pairs L_b = l_A[b] + l_B[b] * 2^16 of stage u of a
+// group, from the group's words: prmt forms the sign-extended 16-bit fields
+// [l_B : l_A], and subtracting 2^16 when l_A < 0 turns the field pair into
+// the integer encoding.
+template <class C, int u>
+VIT_HD void pairs_from_words(const uint32_t (&w)[2][C::U * C::BETA / 4], int (&L)[C::BETA]) {
+#pragma unroll
+  for (int b = 0; b < C::BETA; b++) {
+    const int q = u * C::BETA + b;  // byte of the group
+    const int k = q >> 2, j = q & 3;
+    const uint32_t sel = (uint32_t)j | ((8u | (uint32_t)j) << 4) | ((4u + (uint32_t)j) << 8) |
+                         ((8u | (4u + (uint32_t)j)) << 12);
+    const uint32_t c = prmt(w[0][k], w[1][k], sel);
+    L[b] = (int)(c - ((c & 0x8000u) << 1));
+  }
+}
+
+template <class C>
+VIT_HD void bm_from_pairs(const int (&L)[C::BETA], uint32_t (&D)[C::ND]) {
+#pragma unroll
+  for (int c = 0; c < C::ND; c++) {
+    int acc = 0;
+#pragma unroll
+    for (int b = 0; b < C::BETA; b++) acc += ((c >> b) & 1) ? -L[b] : L[b];
+    D[c] = (uint32_t)acc;
+  }
+}
+
 VIT_HD void store_words(uint32_t* p, const uint32_t* w, int n) {
 #if defined(__CUDA_ARCH__)
   if (n == 4) {
@@ -407,6 +472,19 @@ VIT_HD void fwd_stage(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const Half (
   store_words(sl.base + (int64_t)i * sl.stride, w, C::WORDS);
 }
 
+// Forward stage fed by word loads (every window of the warp has started).
+template <class C, int u>
+VIT_HD void fwd_stage_words(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], int i,
+                            const uint32_t (&w)[2][C::U * C::BETA / 4], Slab sl) {
+  int L[C::BETA];
+  pairs_from_words<C, u>(w, L);
+  uint32_t D[C::ND];
+  bm_from_pairs<C>(L, D);
+  uint32_t wd[C::WORDS];
+  acs_stage<C>(mi, mo, D, wd);
+  store_words(sl.base + (int64_t)i * sl.stride, wd, C::WORDS);
+}
+
 // Traceback step (Alg. 2) of both tiles at iteration i.
 template <class C>
 VIT_HD void tb_stage(int i, const uint32_t (&w)[C::WORDS], int (&s)[2], uint32_t (&acc)[2], const Half (&hw)[2]) {
@@ -432,7 +510,7 @@ VIT_HD void tb_stage(int i, const uint32_t (&w)[C::WORDS], int (&s)[2], uint32_t
 // least every active window length); masked_until: first iteration from which
 // every window of the warp has started.
 template <class C>
-VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t M, Slab sl) {
+VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t M, Slab sl, bool words_ok) {
   uint32_t ma[C::NS], mb[C::NS];
 #pragma unroll
   for (int s = 0; s < C::NS; s++) ma[s] = 0x80008000u;
@@ -442,16 +520,52 @@ VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t 
 
   static_assert(C::U == 2, "two register arrays alternate");
   const int ngroups = Lw / C::U;
-  LlrGroup<C> cur, nxt;
-  load_group<C>(hw, 0, cur);
-  for (int g = 0; g < ngroups; g++) {
-    const int i0 = g * C::U;
-    if (g + 1 < ngroups) load_group<C>(hw, i0 + C::U, nxt);  // prefetch the next group
-    const bool masked = i0 < masked_until;
-    fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl);
-    fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl);
-    if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
-    cur = nxt;
+  bool words = false;
+  if constexpr (kWordLoads<C>) words = words_ok;
+  if (words) {
+    if constexpr (kWordLoads<C>) {
+      // groups before every window has started: byte loads, masked
+      int g = 0;
+      for (; g < ngroups && g * C::U < masked_until; g++) {
+        const int i0 = g * C::U;
+        LlrGroup<C> lg;
+        load_group<C>(hw, i0, lg);
+        fwd_stage<C>(ma, mb, hw, i0, true, M, lg.v[0], sl);
+        fwd_stage<C>(mb, ma, hw, i0 + 1, true, M, lg.v[1], sl);
+        if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
+      }
+      constexpr int NW = C::U * C::BETA / 4;
+      uint32_t wc[2][NW], wn[2][NW];
+      if (g < ngroups) load_group_words<C>(hw, g * C::U, wc);
+      for (; g < ngroups; g++) {
+        const int i0 = g * C::U;
+        if (g + 1 < ngroups) load_group_words<C>(hw, i0 + C::U, wn);  // prefetch the next group
+        fwd_stage_words<C, 0>(ma, mb, i0, wc, sl);
+        fwd_stage_words<C, 1>(mb, ma, i0 + 1, wc, sl);
+        if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+          for (int k = 0; k < NW; k++) wc[h][k] = wn[h][k];
+      }
+    }
+  } else {
+    LlrGroup<C> cur, nxt;
+    load_group<C>(hw, 0, cur);
+    for (int g = 0; g < ngroups; g++) {
+      const int i0 = g * C::U;
+      if (g + 1 < ngroups) {  // prefetch the next group
+        if (i0 + C::U < masked_until)
+          load_group<C>(hw, i0 + C::U, nxt);
+        else
+          load_group_fast<C>(hw, i0 + C::U, nxt);
+      }
+      const bool masked = i0 < masked_until;
+      fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl);
+      fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl);
+      if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
+      cur = nxt;
+    }
   }
 
   // traceback start (Alg. 2): best final metric, ties to the lowest state

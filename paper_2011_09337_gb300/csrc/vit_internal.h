@@ -75,8 +75,16 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
   Slab sl{a.slab + task * a.task_words + lane * C::WORDS, 32 * C::WORDS};
+  // word loads need every active tile's groups to start on 4-byte boundaries
+  bool aligned = true;
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+    if (hw[h].active)
+      aligned = aligned && ((reinterpret_cast<uintptr_t>(hw[h].llr) +
+                             (uintptr_t)((hw[h].t0 - hw[h].start) * C::BETA)) % 4u == 0u);
+  const bool words_ok = __all_sync(0xffffffffu, aligned);
   if constexpr (C::G == 1)
-    decode_pair<C>(hw, Lw, mu, a.M, sl);
+    decode_pair<C>(hw, Lw, mu, a.M, sl, words_ok);
   else
     decode_pair_rot<C>(hw, Lw, mu, a.M, sl, lane);
 }

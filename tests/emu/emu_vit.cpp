@@ -35,10 +35,16 @@ static int emu(const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v2, 
           if (hw[l][h].start + 1 > masked_until) masked_until = hw[l][h].start + 1;
         }
     std::vector<uint32_t> slab((size_t)Lw * C::WORDS);
+    bool words = true;  // the kernel's warp-wide alignment vote
+    for (int l = 0; l < 32; l++)
+      for (int h = 0; h < 2; h++)
+        if (hw[l][h].active)
+          words = words && ((reinterpret_cast<uintptr_t>(hw[l][h].llr) +
+                             (uintptr_t)((hw[l][h].t0 - hw[l][h].start) * C::BETA)) % 4u == 0u);
     for (int l = 0; l < 32; l++) {
       if (!hw[l][0].active && !hw[l][1].active) continue;
       Slab sl{slab.data(), C::WORDS};
-      decode_pair<C>(hw[l], Lw, masked_until, (uint32_t)M, sl);
+      decode_pair<C>(hw[l], Lw, masked_until, (uint32_t)M, sl, words);
     }
   }
   return 0;
