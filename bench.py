@@ -166,6 +166,19 @@ class ClockSampler:
                 "source": "nvml" if self._nvml is not None else "nvidia-smi"}
 
 
+def aggregate(total_ms: float, steps: int, bits_per_rank_step: int, world: int, device) -> tuple[float, float]:
+    """Whole-job throughput: every rank decodes its own shard (weak scaling);
+    the step time is the maximum over ranks, the bits are summed."""
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / steps
+    return ms, bits_per_rank_step * world / (ms * 1e-3) / 1e6
+
+
 def make_inputs(vit, code, device, torch, count=len(EBN0)):
     """LLR streams (int8, stage-major), encoded by the library's encoder."""
     from paper_2011_09337_gb300 import synth
@@ -356,6 +369,47 @@ def mixed_batch_leg(vit, torch, device, steps):
     }
 
 
+LARGE_WORKLOAD = ("2^26-bit streams: K=9 r1/2 (561,753) f=2048 v=96; K=7 (171,133) punctured to r3/4 "
+                  "[110;101] f=2048 v=64; int8 LLRs at Eb/N0 4 dB")
+
+
+def large_streams_leg(vit, torch, device, steps):
+    """The 2^26-bit streams: one decode launch each (plus de-puncturing)."""
+    from paper_2011_09337_gb300 import synth
+
+    n = 1 << 26
+    out = {}
+    cases = [("k9", synth.CODE_K9_R12, 2048, 96, None), ("k7_r34", synth.CODE_K7_R12, 2048, 64, synth.PUNCT_R34)]
+    for name, (K, beta, polys), f, v, mask in cases:
+        code = vit.Code(K, beta, polys, f=f, v=v, puncture=mask)
+
+        def enc(bits):
+            return vit.encode(code, torch.from_numpy(bits).to(device)).cpu().numpy()
+
+        st = synth.make_stream(enc, beta, n, 4.0, seed=4 + len(out), mask=mask)
+        llr = torch.from_numpy(st.llr.reshape(-1)).to(device)
+        ws = torch.empty(code.workspace_bytes(n), dtype=torch.uint8, device=device)
+        o = torch.empty((n + 7) // 8, dtype=torch.uint8, device=device)
+        for _ in range(3):
+            vit.decode(code, llr, n, out=o, workspace=ws)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            vit.decode(code, llr, n, out=o, workspace=ws)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        S = 1 << (K - 1)
+        ops = 4.0 * S * sum(min(n, (t + 1) * f + v) - max(0, t * f - v) for t in range(n // f))
+        got = synth.unpack_bits(o.cpu().numpy(), n)
+        out[name] = {"value": n / (ms * 1e-3) / 1e6, "unit": "Mbit/s", "ms_per_step": ms,
+                     "alu_tops": ops / (ms * 1e-3) / 1e12, "ber": float(np.mean(got != st.bits))}
+        del llr, ws, o
+    out["workload"] = LARGE_WORKLOAD
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,6 +418,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-code batch leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2^26-bit stream leg")
     ap.add_argument("--profile", action="store_true",
                     help="build the workload with --streams streams, run the planned batch twice and exit "
                          "(the target of the ncu captures)")
@@ -425,13 +480,8 @@ def main():
         barrier()
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
     bits_per_step = NBITS * len(streams)
-    value = bits_per_step * world / (ms_per_step * 1e-3) / 1e6
+    ms_per_step, value = aggregate(total_ms, args.steps, bits_per_step, world, dev)
 
     # parity spot check of this run's output against the transmitted bits (BER sanity)
     from paper_2011_09337_gb300 import synth
@@ -477,6 +527,7 @@ def main():
     e2e_value = bits_per_step * world / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
 
     mixed = None if args.no_mixed else mixed_batch_leg(vit, torch, dev, args.steps)
+    large = None if args.no_large else large_streams_leg(vit, torch, dev, max(3, args.steps // 4))
 
     if rank != 0:
         if world > 1:
@@ -508,6 +559,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": args.steps,
         "batch_mixed": mixed,
+        "large_streams": large,
         "ber_6db": ber6,
     }
     if clocks.get("sm_mhz"):

@@ -66,8 +66,16 @@ struct Code {
   // stages per unrolled group: two alternating register arrays (one lane per
   // pair) or the K-1 phases of the rotating slot map (several lanes per pair)
   static constexpr int U = (G == 1) ? 2 : KM1;
-  // renormalise every RN groups (at most 16 stages keeps every field in range)
-  static constexpr int RN = (G == 1) ? 6 : (16 / KM1);
+  // Renormalise every RN groups.  Path metrics of one tile spread by at most
+  // SPREAD = M + 2(K-2)*127*beta < 4(K-1)*127*beta + 1 (M: the finite
+  // -infinity of a known start), and each stage moves a metric by at most
+  // DMAX = 127*beta, so RN*U stages keep every candidate within
+  // SPREAD + (RN*U + 1)*DMAX <= 2^15 - 1 of the reference state.
+  static constexpr int DMAX = 127 * B_;
+  static constexpr int SPREAD = 4 * KM1 * 127 * B_ + 1;
+  static constexpr int RN_MAX = ((32767 - SPREAD) / DMAX - 1) / U;
+  static constexpr int RN = RN_MAX < 1 ? 1 : (RN_MAX > 32 ? 32 : RN_MAX);
+  static_assert(SPREAD + 2 * DMAX < 32768, "decision differences must fit 16 bits");
   static VIT_CX uint32_t poly(int b) { return b == 0 ? G0 : b == 1 ? G1 : b == 2 ? G2 : G3; }
   // branch output alpha_out for register word R (Eq. 1), bit b = coded bit b
   static VIT_CX uint32_t aout(uint32_t R) {
@@ -128,15 +136,22 @@ VIT_HD int ld_s8(const int8_t* p) {
 // ------------------------------------------------------- branch metrics
 // delta_c for coded pattern c (Eq. 2) from the ND magnitudes D[c'] (c' with
 // top bit 0): delta_{~c} = -delta_c.
+// Branch metrics of one stage: D[c'] for the patterns c' with top bit 0,
+// integer encoded for both tiles.
 template <class C>
-VIT_HD uint32_t add_bm(uint32_t m, const uint32_t (&D)[C::ND], uint32_t c) {
-  return ((c >> (C::BETA - 1)) & 1u) ? m - D[(~c) & (C::ND - 1)] : m + D[c];
+struct StageBM {
+  uint32_t D[C::ND];
+};
+
+template <class C>
+VIT_HD uint32_t add_bm(uint32_t m, const StageBM<C>& bm, uint32_t c) {
+  return ((c >> (C::BETA - 1)) & 1u) ? m - bm.D[(~c) & (C::ND - 1)] : m + bm.D[c];
 }
 
 // Packs the stage's LLRs of both tiles (int8, sign-extended) as
 // L_b = l_A[b] + l_B[b] * 2^16 and forms D[c'] = sum_b (-1)^{c'_b} L_b.
 template <class C>
-VIT_HD void stage_bm(const int (&lA)[C::BETA], const int (&lB)[C::BETA], uint32_t (&D)[C::ND]) {
+VIT_HD void stage_bm(const int (&lA)[C::BETA], const int (&lB)[C::BETA], StageBM<C>& D) {
   int L[C::BETA];
 #pragma unroll
   for (int b = 0; b < C::BETA; b++) L[b] = lA[b] + lB[b] * 65536;
@@ -145,7 +160,7 @@ VIT_HD void stage_bm(const int (&lA)[C::BETA], const int (&lB)[C::BETA], uint32_
     int acc = 0;
 #pragma unroll
     for (int b = 0; b < C::BETA; b++) acc += ((c >> b) & 1) ? -L[b] : L[b];
-    D[c] = (uint32_t)acc;
+    D.D[c] = (uint32_t)acc;
   }
 }
 
@@ -174,7 +189,7 @@ VIT_HD int surv_pos(int s) {
 // One radix-2 butterfly (Eq. 3, Eq. 4): predecessors 2x (even) and 2x+1
 // (odd) of mi give successors x and x + S/2 in mo, with their decision words.
 template <class C>
-VIT_HD void butterfly(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const uint32_t (&D)[C::ND], int x,
+VIT_HD void butterfly(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const StageBM<C>& D, int x,
                       uint32_t& E0, uint32_t& E1) {
   constexpr int H = C::NS / 2;
   const uint32_t i0 = 2u * (uint32_t)x;
@@ -200,7 +215,7 @@ VIT_HD void gather2(uint32_t (&w)[C::WORDS], int s, uint32_t Es, uint32_t Ep) {
 // that the two states each prmt combines (s, s + HALFP) are finished
 // together, which keeps few decision words live.
 template <class C>
-VIT_HD void acs_stage(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const uint32_t (&D)[C::ND],
+VIT_HD void acs_stage(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const StageBM<C>& D,
                       uint32_t (&w)[C::WORDS]) {
   constexpr int H = C::NS / 2;
   constexpr int HP = C::HALFP;
@@ -401,13 +416,13 @@ VIT_HD void pairs_from_words(const uint32_t (&w)[2][C::U * C::BETA / 4], int (&L
 }
 
 template <class C>
-VIT_HD void bm_from_pairs(const int (&L)[C::BETA], uint32_t (&D)[C::ND]) {
+VIT_HD void bm_from_pairs(const int (&L)[C::BETA], StageBM<C>& D) {
 #pragma unroll
   for (int c = 0; c < C::ND; c++) {
     int acc = 0;
 #pragma unroll
     for (int b = 0; b < C::BETA; b++) acc += ((c >> b) & 1) ? -L[b] : L[b];
-    D[c] = (uint32_t)acc;
+    D.D[c] = (uint32_t)acc;
   }
 }
 
@@ -465,7 +480,7 @@ VIT_HD void fwd_stage(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const Half (
     for (int h = 0; h < 2; h++)
       if (hw[h].known && i == hw[h].start) init_half<C>(mi, h, true, M);
   }
-  uint32_t D[C::ND];
+  StageBM<C> D;
   stage_bm<C>(lA, lB, D);
   uint32_t w[C::WORDS];
   acs_stage<C>(mi, mo, D, w);
@@ -478,7 +493,7 @@ VIT_HD void fwd_stage_words(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], int i,
                             const uint32_t (&w)[2][C::U * C::BETA / 4], Slab sl) {
   int L[C::BETA];
   pairs_from_words<C, u>(w, L);
-  uint32_t D[C::ND];
+  StageBM<C> D;
   bm_from_pairs<C>(L, D);
   uint32_t wd[C::WORDS];
   acs_stage<C>(mi, mo, D, wd);
@@ -650,7 +665,7 @@ __device__ __forceinline__ uint32_t lane_flip_mask(int lig) {
 }
 
 template <class C, int P>
-__device__ __forceinline__ void rot_butterfly(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND], int a, uint32_t& Ea,
+__device__ __forceinline__ void rot_butterfly(uint32_t (&m)[C::NS], const StageBM<C>& D, int a, uint32_t& Ea,
                                               uint32_t& Eb) {
   const int b = a | (1 << P);
   const uint32_t i0 = rotr_w((uint32_t)a, P, C::KM1);  // register part of the even predecessor
@@ -667,7 +682,7 @@ __device__ __forceinline__ void rot_butterfly(uint32_t (&m)[C::NS], const uint32
 // Pair bit P is a register bit: butterflies inside the lane, visited so that
 // each prmt pair (s, s + HALFP) is finished together.
 template <class C, int P>
-__device__ __forceinline__ void rot_local_stage(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND],
+__device__ __forceinline__ void rot_local_stage(uint32_t (&m)[C::NS], const StageBM<C>& D,
                                                 uint32_t (&w)[C::WORDS]) {
   constexpr int B = 1 << P;
   constexpr int H = C::HALFP;
@@ -699,7 +714,7 @@ __device__ __forceinline__ void rot_local_stage(uint32_t (&m)[C::NS], const uint
 // decision polarity of the lane holding the odd slot is reversed (constant
 // cb), which the traceback undoes.
 template <class C, int P>
-__device__ __forceinline__ void rot_cross_stage(uint32_t (&m)[C::NS], const uint32_t (&D)[C::ND],
+__device__ __forceinline__ void rot_cross_stage(uint32_t (&m)[C::NS], const StageBM<C>& D,
                                                 uint32_t (&w)[C::WORDS], int lig) {
   constexpr int H = C::HALFP;
   const int xm = 1 << (P - C::NSB);
@@ -728,7 +743,7 @@ __device__ __forceinline__ void rot_cross_stage(uint32_t (&m)[C::NS], const uint
 // Branch magnitudes of one stage with the lane's pattern offset for phase P.
 template <class C, int P>
 __device__ __forceinline__ void rot_stage_bm(int (&lA)[C::BETA], int (&lB)[C::BETA], uint32_t flip,
-                                             uint32_t (&D)[C::ND]) {
+                                             StageBM<C>& D) {
 #pragma unroll
   for (int b = 0; b < C::BETA; b++) {
     const int sgn = 1 - 2 * (int)((flip >> (C::BETA * P + b)) & 1u);
@@ -775,7 +790,7 @@ __device__ __forceinline__ void rot_fwd_stage(uint32_t (&m)[C::NS], const Half (
     for (int h = 0; h < 2; h++)
       if (hw[h].known && i == hw[h].start) rot_init_half<C>(m, h, M, lig);
   }
-  uint32_t D[C::ND];
+  StageBM<C> D;
   rot_stage_bm<C, P>(lA, lB, flip, D);
   uint32_t w[C::WORDS];
   if constexpr (P < C::NSB)
@@ -787,6 +802,36 @@ __device__ __forceinline__ void rot_fwd_stage(uint32_t (&m)[C::NS], const Half (
   for (int h = 0; h < 2; h++)
 #pragma unroll
     for (int b = 0; b < C::BETA; b++) cur[h][b] = nxt[h][b];
+}
+
+// Word-fed stage of the rotating layout (every window of the warp started).
+template <class C, int P>
+__device__ __forceinline__ void rot_fwd_stage_words(uint32_t (&m)[C::NS], int i,
+                                                    const uint32_t (&w)[2][C::U * C::BETA / 4], uint32_t flip,
+                                                    int lig, Slab sl) {
+  int L[C::BETA];
+  pairs_from_words<C, P>(w, L);
+#pragma unroll
+  for (int b = 0; b < C::BETA; b++)
+    if ((flip >> (C::BETA * P + b)) & 1u) L[b] = -L[b];
+  StageBM<C> D;
+  bm_from_pairs<C>(L, D);
+  uint32_t wd[C::WORDS];
+  if constexpr (P < C::NSB)
+    rot_local_stage<C, P>(m, D, wd);
+  else
+    rot_cross_stage<C, P>(m, D, wd, lig);
+  store_words(sl.base + (int64_t)i * sl.stride, wd, C::WORDS);
+}
+
+template <class C, int P>
+__device__ __forceinline__ void rot_fwd_group_words(uint32_t (&m)[C::NS], int i0,
+                                                    const uint32_t (&w)[2][C::U * C::BETA / 4], uint32_t flip,
+                                                    int lig, Slab sl) {
+  if constexpr (P < C::KM1) {
+    rot_fwd_stage_words<C, P>(m, i0 + P, w, flip, lig, sl);
+    rot_fwd_group_words<C, P + 1>(m, i0, w, flip, lig, sl);
+  }
 }
 
 template <class C, int P>
@@ -802,7 +847,8 @@ __device__ __forceinline__ void rot_fwd_group(uint32_t (&m)[C::NS], const Half (
 // Decodes the tile pair of a group of G lanes; lig = lane in group.  Lane
 // lig = h (h < 2) traces and emits tile h.
 template <class C>
-__device__ void decode_pair_rot(const Half (&hw)[2], int Lw, int masked_until, uint32_t M, Slab sl, int lane) {
+__device__ void decode_pair_rot(const Half (&hw)[2], int Lw, int masked_until, uint32_t M, Slab sl, int lane,
+                                bool words_ok) {
   const int lig = lane & (C::G - 1);
   const int gbase = lane & ~(C::G - 1);
   const uint32_t flip = lane_flip_mask<C>(lig);
@@ -813,15 +859,42 @@ __device__ void decode_pair_rot(const Half (&hw)[2], int Lw, int masked_until, u
   for (int h = 0; h < 2; h++)
     if (hw[h].known && hw[h].start == 0) rot_init_half<C>(m, h, M, lig);
   const int ngroups = Lw / C::U;
-  int cur[2][C::BETA], nxt[2][C::BETA];
-  load_stage<C>(hw, 0, cur);
-  for (int g = 0; g < ngroups; g++) {
-    const int i0 = g * C::U;
-    rot_fwd_group<C, 0>(m, hw, i0, i0 < masked_until, M, cur, nxt, Lw, flip, lig, sl);
-    if ((g % C::RN) == C::RN - 1) {
+  int g = 0;
+  auto renorm_group = [&](int gg) {
+    if ((gg % C::RN) == C::RN - 1) {
       const uint32_t ref = __shfl_sync(0xffffffffu, m[0], gbase);  // state 0 is slot 0 of the group
 #pragma unroll
       for (int r = 0; r < C::NS; r++) m[r] = m[r] - ref + 0x80008000u;
+    }
+  };
+  if (!(kWordLoads<C> && words_ok)) {
+    int cur[2][C::BETA], nxt[2][C::BETA];
+    load_stage<C>(hw, 0, cur);
+    for (; g < ngroups; g++) {
+      const int i0 = g * C::U;
+      rot_fwd_group<C, 0>(m, hw, i0, i0 < masked_until, M, cur, nxt, Lw, flip, lig, sl);
+      renorm_group(g);
+    }
+  } else if constexpr (kWordLoads<C>) {
+    // groups before every window has started: byte loads, masked
+    for (; g < ngroups && g * C::U < masked_until; g++) {
+      int cur[2][C::BETA], nxt[2][C::BETA];
+      load_stage<C>(hw, g * C::U, cur);
+      rot_fwd_group<C, 0>(m, hw, g * C::U, true, M, cur, nxt, Lw, flip, lig, sl);
+      renorm_group(g);
+    }
+    constexpr int NW = C::U * C::BETA / 4;
+    uint32_t wc[2][NW], wn[2][NW];
+    if (g < ngroups) load_group_words<C>(hw, g * C::U, wc);
+    for (; g < ngroups; g++) {
+      const int i0 = g * C::U;
+      if (g + 1 < ngroups) load_group_words<C>(hw, i0 + C::U, wn);  // prefetch the next group
+      rot_fwd_group_words<C, 0>(m, i0, wc, flip, lig, sl);
+      renorm_group(g);
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int k = 0; k < NW; k++) wc[h][k] = wn[h][k];
     }
   }
 

@@ -86,7 +86,7 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane)
   if constexpr (C::G == 1)
     decode_pair<C>(hw, Lw, mu, a.M, sl, words_ok);
   else
-    decode_pair_rot<C>(hw, Lw, mu, a.M, sl, lane);
+    decode_pair_rot<C>(hw, Lw, mu, a.M, sl, lane, words_ok);
 }
 
 // One warp per task, tasks in launch order.

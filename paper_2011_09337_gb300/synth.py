@@ -97,7 +97,7 @@ def make_stream(encode: Encoder, beta: int, n: int, ebn0_db: float, seed: int, m
     coded = encode(bits)
     if mask is not None:
         sym = puncture(coded, mask)
-        rate = punctured_rate(mask) / beta
+        rate = punctured_rate(mask)  # info bits per transmitted symbol
     else:
         sym = coded.reshape(-1)
         rate = 1.0 / beta

@@ -387,3 +387,13 @@ def test_channel_noise_variance():
     y = synth.bpsk_awgn(np.zeros(200000, np.uint8), sigma, synth.rng(0))
     assert np.mean(y) == pytest.approx(1.0, abs=0.01)
     assert np.std(y) == pytest.approx(sigma, rel=0.01)
+
+
+def test_punctured_stream_noise_uses_the_punctured_rate():
+    """Eb/N0 is energy per information bit: a rate-3/4 stream carries 3/4 of a
+    bit per transmitted symbol, so sigma^2 = 1 / (2 * 3/4 * Eb/N0)."""
+    mask = np.array(synth.PUNCT_R34)
+    assert synth.punctured_rate(mask) == pytest.approx(0.75)
+    s = synth.make_stream(lambda x: np.zeros((x.size, 2), np.uint8), 2, 3000, 4.0, seed=1, mask=mask)
+    assert s.sigma ** 2 == pytest.approx(1 / (2 * 0.75 * 10 ** 0.4))
+    assert s.llr.size == synth.kept_symbols(3000, mask) == 4000
