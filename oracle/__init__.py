@@ -13,6 +13,13 @@ Functions and the passage each one follows:
 * :func:`viterbi_blocked`   Eq. 2-4 with Alg. 1 (forward) and Alg. 2 (traceback),
                             run on the overlapped tiles of Fig. relworks;
                             ``f=0`` is the full-frame decoder.
+* :func:`viterbi_blocked_pt` the same tiles with the first parallel traceback
+                            of Sec. "Parallel Traceback Algorithm" (Fig. pt1):
+                            subframes of ``f0`` stages, each traced back from
+                            ``v2`` stages to its right, starting at the stored
+                            argmax state or at a SplitMix64 state.
+* :func:`viterbi_window`    one window with an explicit traceback start state.
+* :func:`splitmix64`        the counter-based generator of the random start.
 * :func:`viterbi_full`      the same with one tile.
 * :func:`brute_force_ml`    exhaustive maximum-likelihood search (pin only).
 * :func:`metric_hard`,
@@ -68,6 +75,11 @@ def _load():
             lib.orc_depuncture.argtypes = [vp, i64, i64, i32, vp, i32, vp]
             lib.orc_depuncture.restype = i64
             lib.orc_viterbi_blocked.argtypes = [i32, i32, vp, vp, i64, i64, i64, i64, i32, i64, i64, i64, vp, vp]
+            lib.orc_viterbi_blocked_pt.argtypes = [i32, i32, vp, vp, i64, i64, i64, i64, i64, i32,
+                                                   ctypes.c_uint64, i32, i64, i64, i64, vp]
+            lib.orc_viterbi_window.argtypes = [i32, i32, vp, vp, i64, i64, i32, i64, i32, i64, i64, vp]
+            lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            lib.orc_splitmix64.restype = ctypes.c_uint64
             lib.orc_brute_force.argtypes = [i32, i32, vp, vp, i32, i32, vp, vp, vp]
             lib.orc_metric_hard.argtypes = [i32, i32, vp, vp, i64, vp, vp]
             lib.orc_metric_lse.argtypes = [i32, i32, vp, vp, i64, ctypes.c_double, vp, vp]
@@ -140,6 +152,51 @@ def viterbi_blocked(K: int, beta: int, polys: Sequence[int], llr: np.ndarray, f:
     if return_metrics:
         return bits, metrics[: b1 - b0]
     return bits
+
+
+PT_STORED, PT_RANDOM = 0, 1
+
+
+def viterbi_blocked_pt(K: int, beta: int, polys: Sequence[int], llr: np.ndarray, f: int, v1: int, v2: int,
+                       f0: int, start: int = PT_STORED, seed: int = 0, mode: int = STREAM, M: int = M_DEFAULT,
+                       blocks: tuple[int, int] | None = None):
+    """Blocked decoder with the parallel traceback (subframes of ``f0`` stages,
+    overlap ``v2``; ``start`` = PT_STORED or PT_RANDOM).  Returns one bit per
+    stage like :func:`viterbi_blocked`."""
+    lib = _load()
+    x = np.ascontiguousarray(llr, dtype=np.int8).reshape(-1)
+    if x.size % beta:
+        raise ValueError("LLR count is not a multiple of beta")
+    n = x.size // beta
+    p = _polys(K, beta, polys)
+    bits = np.zeros(n, dtype=np.uint8)
+    fb = n if (f == 0 or f > n) else f
+    nb = (n + fb - 1) // fb if n else 0
+    b0, b1 = (0, nb) if blocks is None else blocks
+    _check(lib.orc_viterbi_blocked_pt(K, beta, _ptr(p), _ptr(x), n, f, v1, v2, f0, start, seed, mode, M, b0, b1,
+                                      _ptr(bits)), "viterbi_blocked_pt")
+    return bits
+
+
+def viterbi_window(K: int, beta: int, polys: Sequence[int], llr: np.ndarray, t0: int, t1: int, known: bool,
+                   end_state: int = -1, emit: tuple[int, int] | None = None, M: int = M_DEFAULT) -> np.ndarray:
+    """One window [t0, t1) of the stream (Alg. 1 + Alg. 2) with an explicit
+    traceback start state (-1: argmax).  Returns n bits; only ``emit``
+    (default: the whole window) is written."""
+    lib = _load()
+    x = np.ascontiguousarray(llr, dtype=np.int8).reshape(-1)
+    n = x.size // beta
+    p = _polys(K, beta, polys)
+    bits = np.zeros(n, dtype=np.uint8)
+    e0, e1 = (t0, t1) if emit is None else emit
+    _check(lib.orc_viterbi_window(K, beta, _ptr(p), _ptr(x), t0, t1, int(known), M, end_state, e0, e1, _ptr(bits)),
+           "viterbi_window")
+    return bits
+
+
+def splitmix64(seed: int, i: int) -> int:
+    """Output ``i`` (0-based) of SplitMix64 seeded with ``seed``."""
+    return int(_load().orc_splitmix64(seed, i))
 
 
 def viterbi_full(K: int, beta: int, polys: Sequence[int], llr: np.ndarray, mode: int = STREAM,

@@ -13,6 +13,9 @@
  *   tiling ............. Sec. "Previous GPU methods", Fig. relworks: blocks of
  *                        f output stages with v1/v2 overlaps
  *   de-puncturing ...... Sec. "De-puncturing": zero LLR at removed positions
+ *   parallel traceback . Sec. "Parallel Traceback Algorithm" (Fig. pt1):
+ *                        subframes of f0 stages, each traced back from v2
+ *                        stages to its right
  * plus two quantities the paper does not define (best-path metric and its
  * temperature log-sum-exp relaxation, with gradients) and brute-force ML.
  *
@@ -209,6 +212,150 @@ int orc_viterbi_blocked(int K, int beta, const uint32_t* polys, const int8_t* ll
     if (metric_out) metric_out[b - b_begin] = m;
   }
   free(aout);
+  return rc;
+}
+
+/*
+ * One window [t0, t1) of a de-punctured stream (Alg. 1 then Alg. 2) with an
+ * explicit traceback start: end_state >= 0 starts there, -1 at the argmax of
+ * the last stage.  known != 0 starts in state 0 (others -M), else all 0.
+ * Bits of stages [e0, e1) are written to bits[t] (global stage index).
+ */
+int orc_viterbi_window(int K, int beta, const uint32_t* polys, const int8_t* llr, int64_t t0, int64_t t1, int known,
+                       int64_t M, int end_state, int64_t e0, int64_t e1, uint8_t* bits) {
+  if (!code_ok(K, beta, polys) || t0 < 0 || t1 <= t0 || M <= 0 || !llr || !bits) return ORC_EINVAL;
+  if (end_state >= (1 << (K - 1)) || end_state < -1) return ORC_EINVAL;
+  uint32_t* aout = NULL;
+  if (make_aout(K, beta, polys, &aout)) return ORC_ENOMEM;
+  const int rc = run_window(K, beta, polys, aout, llr, t0, t1, known, M, end_state, e0, e1, bits, NULL);
+  free(aout);
+  return rc;
+}
+
+/* ------------------------------------------------- parallel traceback */
+/*
+ * SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014) used as a counter-based generator: output i under
+ * key `seed` is the mix of seed + (i + 1) * 0x9E3779B97F4A7C15 (the state the
+ * sequential generator seeded with `seed` holds before its (i+1)-th output).
+ */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+#define ORC_PT_STORED 0
+#define ORC_PT_RANDOM 1
+
+/*
+ * Blocked decoding with the paper's first parallel traceback (Sec. "Parallel
+ * Traceback Algorithm", Fig. pt1).  Block b's windows are those of
+ * orc_viterbi_blocked.  Its emitted range [e0, e1) is cut into subframes of
+ * f0 stages: subframe k emits [e0 + k f0, min(e0 + (k+1) f0, e1)).  Subframe
+ * k overlaps its right-hand neighbour by v2 stages: its traceback starts at
+ * stage u = min(end_k + v2, t1) - 1 and runs down to the subframe's first
+ * stage, emitting only the subframe's own stages.  Its start state is
+ *   - the window's usual start (Alg. 2 argmax, or state 0 at the end of a
+ *     terminated frame) when u is the window's last stage;
+ *   - otherwise, with ORC_PT_STORED, the argmax of the path metrics of stage
+ *     u (ties to the lowest state), recorded during the forward pass; with
+ *     ORC_PT_RANDOM, the top K-1 bits of orc_splitmix64(seed, u).
+ * f0 == 0 or f0 >= the block's emitted length gives the serial traceback.
+ */
+int orc_viterbi_blocked_pt(int K, int beta, const uint32_t* polys, const int8_t* llr, int64_t n, int64_t f,
+                           int64_t v1, int64_t v2, int64_t f0, int start_rule, uint64_t seed, int mode, int64_t M,
+                           int64_t b_begin, int64_t b_end, uint8_t* bits) {
+  if (!code_ok(K, beta, polys) || n < 0 || f < 0 || v1 < 0 || v2 < 0 || f0 < 0 || M <= 0) return ORC_EINVAL;
+  if (mode != ORC_STREAM && mode != ORC_TERMINATED && mode != ORC_FREE_START) return ORC_EINVAL;
+  if (start_rule != ORC_PT_STORED && start_rule != ORC_PT_RANDOM) return ORC_EINVAL;
+  if (n == 0) return ORC_OK;
+  if (!llr || !bits) return ORC_EINVAL;
+  const int S = 1 << (K - 1);
+  const int64_t fb = (f == 0 || f > n) ? n : f;
+  const int64_t B = (n + fb - 1) / fb;
+  if (b_end < 0 || b_end > B) b_end = B;
+  if (b_begin < 0) b_begin = 0;
+  uint32_t* aout = NULL;
+  if (make_aout(K, beta, polys, &aout)) return ORC_ENOMEM;
+  const int64_t Lmax = fb + v1 + v2;
+  const int64_t sub = (f0 == 0 || f0 > fb) ? fb : f0;
+  const int64_t nsub_max = (fb + sub - 1) / sub;
+  int64_t* pm = (int64_t*)malloc(sizeof(int64_t) * S);
+  int64_t* nm = (int64_t*)malloc(sizeof(int64_t) * S);
+  uint8_t* dec = (uint8_t*)malloc((size_t)((Lmax * S + 7) / 8 + 1));
+  int64_t* ustage = (int64_t*)malloc(sizeof(int64_t) * nsub_max);
+  int* ustate = (int*)malloc(sizeof(int) * nsub_max);
+  int rc = ORC_OK;
+  if (!pm || !nm || !dec || !ustage || !ustate) rc = ORC_ENOMEM;
+  for (int64_t b = b_begin; b < b_end && rc == ORC_OK; b++) {
+    const int64_t e0 = b * fb, e1 = (e0 + fb < n) ? e0 + fb : n;
+    const int64_t t0 = (e0 - v1 > 0) ? e0 - v1 : 0;
+    const int64_t t1 = (e1 + v2 < n) ? e1 + v2 : n;
+    const int known = (t0 == 0 && mode != ORC_FREE_START);
+    const int64_t nsub = (e1 - e0 + sub - 1) / sub;
+    for (int64_t k = 0; k < nsub; k++) {
+      const int64_t end_k = (e0 + (k + 1) * sub < e1) ? e0 + (k + 1) * sub : e1;
+      ustage[k] = ((end_k + v2 < t1) ? end_k + v2 : t1) - 1;
+      ustate[k] = -1;
+    }
+    memset(dec, 0, (size_t)(((t1 - t0) * S + 7) / 8 + 1));
+    for (int j = 0; j < S; j++) pm[j] = known ? (j == 0 ? 0 : -M) : 0;
+    /* forward procedure (Alg. 1, Eq. 2-4) over the window */
+    for (int64_t t = t0; t < t1; t++) {
+      const int8_t* l = llr + t * beta;
+      for (int j = 0; j < S; j++) {
+        const int i0 = (2 * j) & (S - 1), i1 = i0 | 1;
+        const uint32_t R0 = 2u * (uint32_t)j, R1 = R0 + 1u;
+        int64_t bm0 = 0, bm1 = 0;
+        for (int bb = 0; bb < beta; bb++) {
+          bm0 += ((aout[R0] >> bb) & 1u) ? -(int64_t)l[bb] : (int64_t)l[bb];
+          bm1 += ((aout[R1] >> bb) & 1u) ? -(int64_t)l[bb] : (int64_t)l[bb];
+        }
+        const int64_t c0 = pm[i0] + bm0, c1 = pm[i1] + bm1;
+        if (c1 > c0) {
+          nm[j] = c1;
+          dec_set(dec, (t - t0) * S + j, 1);
+        } else {
+          nm[j] = c0;
+        }
+      }
+      int64_t* tmp = pm;
+      pm = nm;
+      nm = tmp;
+      /* record the start state of every subframe whose traceback starts here */
+      for (int64_t k = 0; k < nsub; k++) {
+        if (ustage[k] != t) continue;
+        if (t == t1 - 1 && t1 == n && mode == ORC_TERMINATED) {
+          ustate[k] = 0;
+        } else if (t == t1 - 1 || start_rule == ORC_PT_STORED) {
+          int jm = 0;
+          for (int s2 = 1; s2 < S; s2++)
+            if (pm[s2] > pm[jm]) jm = s2;
+          ustate[k] = jm;
+        } else {
+          ustate[k] = (int)(orc_splitmix64(seed, (uint64_t)t) >> (64 - (K - 1)));
+        }
+      }
+    }
+    /* backward procedure (Alg. 2) once per subframe */
+    for (int64_t k = nsub - 1; k >= 0; k--) {
+      const int64_t s0 = e0 + k * sub;
+      const int64_t s1 = (s0 + sub < e1) ? s0 + sub : e1;
+      int j = ustate[k];
+      for (int64_t t = ustage[k]; t >= s0; t--) {
+        if (t < s1) bits[t] = (uint8_t)((j >> (K - 2)) & 1);
+        j = ((j << 1) | dec_get(dec, (t - t0) * S + j)) & (S - 1);
+      }
+    }
+  }
+  free(aout);
+  free(pm);
+  free(nm);
+  free(dec);
+  free(ustage);
+  free(ustate);
   return rc;
 }
 

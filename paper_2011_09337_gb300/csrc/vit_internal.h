@@ -41,7 +41,7 @@ VIT_HD int64_t find_frame(const int64_t* tile0, int nframes, int64_t gt) {
 #if defined(__CUDACC__)
 // Decodes warp task `task` of one code: 64 / G tiles, lanes grouped G per
 // tile pair.
-template <class C>
+template <class C, bool kWords = true>
 __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane) {
   constexpr int TPT = 64 / C::G;  // tiles per task
   const int pair = lane / C::G;
@@ -82,7 +82,7 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane)
     if (hw[h].active)
       aligned = aligned && ((reinterpret_cast<uintptr_t>(hw[h].llr) +
                              (uintptr_t)((hw[h].t0 - hw[h].start) * C::BETA)) % 4u == 0u);
-  const bool words_ok = __all_sync(0xffffffffu, aligned);
+  const bool words_ok = kWords && __all_sync(0xffffffffu, aligned);
   if constexpr (C::G == 1)
     decode_pair<C>(hw, Lw, mu, a.M, sl, words_ok);
   else
@@ -95,7 +95,7 @@ __global__ void __maxnreg__(kMaxRegs) decode_tiles_kernel(const KArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t task = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (task >= a.ntasks) return;  // warp-uniform
-  run_task<C>(a, task, lane);
+  run_task<C, (C::G == 1)>(a, task, lane);
 }
 
 // Persistent kernel over the tasks of two codes: each warp takes the next
@@ -115,7 +115,7 @@ struct MixArgs {
 // Out-of-line task bodies keep the two codes' register allocations apart.
 template <class C>
 __device__ __noinline__ void run_task_call(const KArgs a, int64_t task, int lane) {
-  run_task<C>(a, task, lane);
+  run_task<C, (C::G == 1)>(a, task, lane);
 }
 
 template <class C0, class C1>
