@@ -90,6 +90,23 @@ int vit_set_puncture(vit_code* code, const uint8_t* mask, int period);
  * or VIT_FREE_START. */
 int vit_set_termination(vit_code* code, int mode);
 
+/*
+ * Parallel traceback (Sec. "Parallel Traceback Algorithm", Fig. pt1): each
+ * tile's emitted stages are cut into subframes of f0 stages, each traced
+ * back on its own from v2 stages to its right (the overlap is not emitted).
+ * A subframe whose traceback starts at its window's last stage starts from
+ * the usual state (argmax, or state 0 at the end of a terminated frame); the
+ * others start from the argmax of their first traceback stage's path
+ * metrics, recorded during the forward pass (VIT_PT_STORED), or from the top
+ * K-1 bits of output u of SplitMix64 seeded with `seed` (VIT_PT_RANDOM; u =
+ * the global index of that stage).  The decoded bits differ from the serial
+ * traceback's.  f0: 0 (off, the default) or a positive multiple of 8.
+ * Returns VIT_EUNSUPPORTED for codes without a compiled parallel-traceback
+ * kernel (those whose 2^(K-1) states do not fit one lane: K > 7).
+ */
+enum { VIT_PT_STORED = 0, VIT_PT_RANDOM = 1 };
+int vit_set_parallel_traceback(vit_code* code, int64_t f0, int rule, uint64_t seed);
+
 void vit_destroy(vit_code* code);
 
 /* Number of int8 LLRs the decoder reads for n trellis stages. */
@@ -140,6 +157,16 @@ int vit_decode_noalloc(const vit_code* code, const int8_t* llr, int64_t n, uint8
  */
 int vit_encode(const vit_code* code, const uint8_t* bits, int64_t n, uint8_t* coded, vit_stream_t stream);
 
+/*
+ * Hard-decision input (Sec. "Hard-decision vs. Soft-decision"): a receiver
+ * that keeps only the sign of each symbol hands the decoder bits.  Expands
+ * `count` received bits (device, packed LSB-first: bit i at byte i >> 3, bit
+ * i & 7) into int8 LLRs (device, `count` bytes): bit 0 -> +1, bit 1 -> -1.
+ * Decoding those LLRs maximises the agreement with the received bits, i.e.
+ * it is minimum-Hamming-distance decoding.  count = vit_llr_count(code, n).
+ */
+int vit_hard_llr(const uint8_t* bits, int64_t count, int8_t* llr, vit_stream_t stream);
+
 /* ----------------------------------------------------------------- batches */
 
 typedef struct {
@@ -151,17 +178,23 @@ typedef struct {
 } vit_frame;
 
 /*
- * Plans a batch: sorts the tiles of all frames by cost, sizes the scratch,
- * uploads the work queue and, when flags has VIT_BATCH_GRAPH, captures the
- * persistent decode launch in a CUDA graph on first run.  Frame pointers are
- * recorded: a plan decodes the same buffers every time it runs.  Tiling uses
- * each frame's code (f, v1, v2), or the autotuned tiling with VIT_BATCH_TUNE.
+ * Plans a batch: groups the frames by (compiled kernel, tiling), orders each
+ * group's frames longest first, sizes the scratch and uploads the frame
+ * tables.  Each group is one launch of its code's tile decoder; the groups
+ * run concurrently (the costliest on the caller's stream, the others on
+ * streams owned by the plan, forked and joined with events).  Frame pointers
+ * are recorded: a plan decodes the same buffers every time it runs.  Tiling
+ * uses each frame's code (f, v1, v2); the autotuner of the Python package
+ * (paper_2011_09337_gb300.tune) picks tilings and CTA sizes by timing plans.
+ *
+ * flags: VIT_BATCH_GRAPH captures the launches in a CUDA graph on the first
+ * run and replays it afterwards.  VIT_BATCH_PERSISTENT: when the batch holds
+ * exactly two code groups for which a persistent two-code kernel is
+ * compiled, one launch pulls all their warp tasks from a queue ordered
+ * longest window first (otherwise ignored).  Bits 8..15 give the CTA size in
+ * warps (1..8, 0 = 4).  Other bits: VIT_EINVAL.
  */
-/* flags: VIT_BATCH_GRAPH captures the launch; bits 8..15 give the CTA size
- * in warps (1..8, 0 = 4).  When the batch holds exactly two code groups for
- * which a persistent two-code kernel is compiled, one launch pulls all their
- * warp tasks from a queue ordered longest window first. */
-enum { VIT_BATCH_GRAPH = 1, VIT_BATCH_TUNE = 2 };
+enum { VIT_BATCH_GRAPH = 1, VIT_BATCH_PERSISTENT = 4 };
 int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int flags);
 int vit_batch_run(vit_batch* batch, vit_stream_t stream);
 void vit_batch_destroy(vit_batch* batch);

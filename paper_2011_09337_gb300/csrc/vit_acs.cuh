@@ -148,6 +148,28 @@ VIT_HD uint32_t add_bm(uint32_t m, const StageBM<C>& bm, uint32_t c) {
   return ((c >> (C::BETA - 1)) & 1u) ? m - bm.D[(~c) & (C::ND - 1)] : m + bm.D[c];
 }
 
+// Signed branch metric of pattern c (integer encoded for both tiles).
+template <class C>
+VIT_HD uint32_t bmv(const StageBM<C>& bm, uint32_t c) {
+  return ((c >> (C::BETA - 1)) & 1u) ? 0u - bm.D[(~c) & (C::ND - 1)] : bm.D[c];
+}
+
+// x + k as one integer multiply-add, x * kOne + k, with the multiplier read
+// from constant memory (1; unknown to the compiler, so the add stays an IMAD
+// and issues on the FMA pipe, leaving the ALU pipe to max, prmt and lop3).
+#if defined(__CUDACC__)
+static __constant__ uint32_t kOne = 1u;
+#endif
+VIT_HD uint32_t add_on_fma(uint32_t x, uint32_t k) {
+#if defined(__CUDA_ARCH__)
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(kOne), "r"(k));
+  return r;
+#else
+  return x + k;
+#endif
+}
+
 // Packs the stage's LLRs of both tiles (int8, sign-extended) as
 // L_b = l_A[b] + l_B[b] * 2^16 and forms D[c'] = sum_b (-1)^{c'_b} L_b.
 template <class C>
@@ -198,7 +220,9 @@ VIT_HD void butterfly(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const 
   const uint32_t x00 = add_bm<C>(mi[2 * x], D, c00), x01 = add_bm<C>(mi[2 * x + 1], D, c01);
   const uint32_t x10 = add_bm<C>(mi[2 * x], D, c10), x11 = add_bm<C>(mi[2 * x + 1], D, c11);
   E0 = x00 - x01 + 0x8000u;
-  E1 = x10 - x11 + 0x8000u;
+  // x10 - x11 = (x00 - x01) + (d(c10) - d(c11) - d(c00) + d(c01)): the
+  // bracket is the same for every butterfly with these patterns this stage
+  E1 = add_on_fma(E0, bmv<C>(D, c10) - bmv<C>(D, c11) - bmv<C>(D, c00) + bmv<C>(D, c01));
   mo[x] = vmaxu2(x00, x01);
   mo[x + H] = vmaxu2(x10, x11);
 }
@@ -521,6 +545,134 @@ VIT_HD void tb_stage(int i, const uint32_t (&w)[C::WORDS], int (&s)[2], uint32_t
   }
 }
 
+// x >> (n mod 32) (funnel shift of x with itself; only the low 5 bits of n
+// are used).
+VIT_HD uint32_t rotr32(uint32_t x, uint32_t n) {
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_r(x, x, n);
+#else
+  n &= 31u;
+  return n ? (x >> n) | (x << (32u - n)) : x;
+#endif
+}
+
+// Byte store to global memory.
+VIT_HD void store_byte(uint8_t* p, uint32_t v) {
+#if defined(__CUDA_ARCH__)
+  asm volatile("st.global.u8 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+#else
+  *p = (uint8_t)v;
+#endif
+}
+
+// Survivor decision of state j (its low K-1 bits) for tile h at one stage.
+// Tile h's bit of state s sits at bit 16h + surv_pos(s) of word surv_word(s);
+// tile 0's bits are stored inverted.  For 64 states one prmt per word pair
+// gathers the tile's 32 bits of states [0, 32) and [32, 64) in state order.
+template <class C>
+VIT_HD uint32_t tb_decision(const uint32_t (&w)[C::WORDS], uint32_t j, int h) {
+  if constexpr (C::WORDS == 4) {
+    const uint32_t sel = h ? 0x7632u : 0x5410u;
+    const uint32_t x = (j & 32u) ? prmt(w[2], w[3], sel) : prmt(w[0], w[1], sel);
+    return (rotr32(x, j) & 1u) ^ (h ? 0u : 1u);
+  } else {
+    const int sj = (int)(j & (uint32_t)(C::S - 1));
+    return ((pick_word<C>(w, sj) >> (16 * h + surv_pos<C>(sj))) & 1u) ^ (h ? 0u : 1u);
+  }
+}
+
+// Asks L2 to fetch the warp's survivor words of stages [i, i + cnt) (one
+// contiguous block of cnt * 32 lanes * WORDS words; lane 0's slab pointer is
+// its start).  No effect on the host build.
+VIT_HD void slab_prefetch_l2(const Slab& sl, int i, int cnt) {
+#if defined(__CUDA_ARCH__)
+  if ((threadIdx.x & 31) == 0 && cnt > 0) {
+    const uint32_t* p = sl.base + (int64_t)i * sl.stride;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((uint32_t)(cnt * sl.stride * 4))
+                 : "memory");
+  }
+#endif
+}
+
+// Traceback (Alg. 2) of two tiles whose windows share their offsets and
+// emit whole bytes: r0/r1 are the first/one-past-last emitted iterations,
+// r1 - r0 a multiple of 8 and r1 + K - 1 <= Lw.  Following a decision d at
+// iteration i gives state (2j + d) mod S, whose bit K-2 after K-1 further
+// steps is d: d is the decoded bit of iteration i - (K-1).  So iterations
+// [r0 + K-1, Lw) are read and each aligned group of 8 emits one byte per tile.
+// Survivor words come from HBM: L2 prefetches run 4 groups ahead and three
+// register buffers hold the current group and the next two.
+template <class C>
+struct TbState {
+  uint32_t j0, j1, acc0, acc1;
+};
+
+template <class C>
+VIT_HD void tb_group(TbState<C>& st, const uint32_t (&w)[8][C::WORDS]) {
+#pragma unroll
+  for (int k = 7; k >= 0; k--) {
+    const uint32_t d0 = tb_decision<C>(w[k], st.j0, 0), d1 = tb_decision<C>(w[k], st.j1, 1);
+    st.j0 = 2u * st.j0 + d0;
+    st.j1 = 2u * st.j1 + d1;
+    st.acc0 = 2u * st.acc0 + d0;
+    st.acc1 = 2u * st.acc1 + d1;
+  }
+}
+
+template <class C>
+VIT_HD void tb_load_group(const Slab& sl, int i, uint32_t (&w)[8][C::WORDS]) {
+#pragma unroll
+  for (int k = 0; k < 8; k++) load_words<C>(sl, i + k, w[k]);
+}
+
+template <class C>
+VIT_HD void traceback_bytes(const Half (&hw)[2], int Lw, int r0, int r1, const int (&s0)[2], Slab sl) {
+  const int ib = r0 + C::KM1;
+  const int nbytes = (r1 - r0) >> 3;
+  TbState<C> st{(uint32_t)s0[0], (uint32_t)s0[1], 0u, 0u};
+  // the partial group above the last whole group of 8 (no emission there)
+  const int top = ib + 8 * ((Lw - ib) >> 3);
+  int q = ((top - ib) >> 3) - 1;  // highest whole group
+  slab_prefetch_l2(sl, ib + 8 * (q - 3 > 0 ? q - 3 : 0), 8 * (q + 1 < 4 ? q + 1 : 4));
+  for (int i = Lw - 1; i >= top; i--) {
+    uint32_t w[C::WORDS];
+    load_words<C>(sl, i, w);
+    st.j0 = 2u * st.j0 + tb_decision<C>(w, st.j0, 0);
+    st.j1 = 2u * st.j1 + tb_decision<C>(w, st.j1, 1);
+  }
+  if (q < 0) return;
+  uint8_t* o0 = hw[0].out + (hw[0].e0 >> 3);
+  uint8_t* o1 = hw[1].out + (hw[1].e0 >> 3);
+  auto emit = [&](int g) {
+    if (g < nbytes) {
+      store_byte(o0 + g, st.acc0 & 0xffu);
+      store_byte(o1 + g, st.acc1 & 0xffu);
+    }
+  };
+  uint32_t b0[8][C::WORDS], b1[8][C::WORDS], b2[8][C::WORDS];
+  tb_load_group<C>(sl, ib + 8 * q, b0);
+  if (q >= 1) tb_load_group<C>(sl, ib + 8 * (q - 1), b1);
+  // invariant at the loop top: b0 holds group q, b1 group q-1 (if q >= 1)
+  while (true) {
+    if (q >= 4) slab_prefetch_l2(sl, ib + 8 * (q - 4), 8);
+    if (q >= 2) tb_load_group<C>(sl, ib + 8 * (q - 2), b2);
+    tb_group<C>(st, b0);
+    emit(q);
+    if (--q < 0) break;
+    if (q >= 4) slab_prefetch_l2(sl, ib + 8 * (q - 4), 8);
+    if (q >= 2) tb_load_group<C>(sl, ib + 8 * (q - 2), b0);
+    tb_group<C>(st, b1);
+    emit(q);
+    if (--q < 0) break;
+    if (q >= 4) slab_prefetch_l2(sl, ib + 8 * (q - 4), 8);
+    if (q >= 2) tb_load_group<C>(sl, ib + 8 * (q - 2), b1);
+    tb_group<C>(st, b2);
+    emit(q);
+    if (--q < 0) break;
+    // b0 holds group q, b1 group q-1: the invariant again
+  }
+}
+
 // Decodes the two tiles of one lane.  Lw: iterations (a multiple of U, at
 // least every active window length); masked_until: first iteration from which
 // every window of the warp has started.
@@ -600,6 +752,17 @@ VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t 
     s[h] = hw[h].end_zero ? 0 : best;
   }
 
+  {
+    const int r0 = hw[0].start + (int)(hw[0].e0 - hw[0].t0);
+    const int r1 = hw[0].start + (int)(hw[0].e1 - hw[0].t0);
+    const bool same = hw[0].active && hw[1].active && hw[0].start == hw[1].start &&
+                      hw[0].e0 - hw[0].t0 == hw[1].e0 - hw[1].t0 && hw[0].e1 - hw[0].t0 == hw[1].e1 - hw[1].t0;
+    if (same && r1 > r0 && ((r1 - r0) & 7) == 0 && r1 + C::KM1 <= Lw) {
+      traceback_bytes<C>(hw, Lw, r0, r1, s, sl);
+      return;
+    }
+  }
+
   // lowest iteration that still emits a bit, over both tiles
   int stop = Lw;
 #pragma unroll
@@ -674,7 +837,7 @@ __device__ __forceinline__ void rot_butterfly(uint32_t (&m)[C::NS], const StageB
   const uint32_t x00 = add_bm<C>(m[a], D, c00), x01 = add_bm<C>(m[b], D, c01);
   const uint32_t x10 = add_bm<C>(m[a], D, c10), x11 = add_bm<C>(m[b], D, c11);
   Ea = x00 - x01 + 0x8000u;
-  Eb = x10 - x11 + 0x8000u;
+  Eb = add_on_fma(Ea, bmv<C>(D, c10) - bmv<C>(D, c11) - bmv<C>(D, c00) + bmv<C>(D, c01));
   m[a] = vmaxu2(x00, x01);
   m[b] = vmaxu2(x10, x11);
 }

@@ -94,6 +94,16 @@ __global__ void encode_kernel(const uint8_t* __restrict__ bits, int64_t n, int K
   for (int b = 0; b < beta; b++) out[t * beta + b] = (uint8_t)(__popc(g[b] & R) & 1);
 }
 
+// Hard-decision input: received bit i (packed LSB-first) -> int8 +1 (bit 0)
+// or -1 (bit 1).  One thread per output byte group of 8 symbols.
+__global__ void hard_llr_kernel(const uint8_t* __restrict__ bits, int64_t count, int8_t* __restrict__ llr) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g * 8 >= count) return;
+  const uint32_t b = bits[g];
+  const int64_t lim = (count - g * 8 < 8) ? count - g * 8 : 8;
+  for (int k = 0; k < lim; k++) llr[g * 8 + k] = ((b >> k) & 1u) ? (int8_t)-1 : (int8_t)1;
+}
+
 bool code_args_ok(int K, int beta, const uint32_t* polys) {
   if (K < 3 || K > 9 || beta < 2 || beta > 4 || polys == nullptr) return false;
   if ((K - 1) * beta > 32) return false;
@@ -145,6 +155,27 @@ using namespace mixreg;
 void register_mixed(const MixKey& a, const MixKey& b, cudaError_t (*launch)(const MixArgs&, int, cudaStream_t)) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   mix_registry().push_back(MixReg{a, b, launch, MixEntry{{nullptr, nullptr}, launch}});
+}
+
+struct PtReg {
+  MixKey key;
+  LaunchFn launch;
+};
+std::vector<PtReg>& pt_registry() {
+  static std::vector<PtReg> r;
+  return r;
+}
+
+void register_pt(const MixKey& k, LaunchFn launch) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  pt_registry().push_back(PtReg{k, launch});
+}
+
+LaunchFn find_pt(const CodeEntry* e) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (const PtReg& r : pt_registry())
+    if (key_matches(r.key, e)) return r.launch;
+  return nullptr;
 }
 
 const MixEntry* find_mixed(const CodeEntry* x, const CodeEntry* y, bool* swapped) {
@@ -244,6 +275,27 @@ int vit_set_termination(vit_code* c, int mode) {
   return VIT_OK;
 }
 
+int vit_set_parallel_traceback(vit_code* c, int64_t f0, int rule, uint64_t seed) {
+  if (int r = check_code(c)) return r;
+  if (f0 < 0 || (f0 % 8) != 0 || f0 > ((int64_t)1 << 30))
+    return fail(VIT_EINVAL, "invalid subframe length f0=%lld (0 or a positive multiple of 8)", (long long)f0);
+  if (rule != VIT_PT_STORED && rule != VIT_PT_RANDOM) return fail(VIT_EINVAL, "invalid traceback start rule");
+  if (f0 == 0) {
+    c->pt_f0 = 0;
+    c->pt_launch = nullptr;
+    return VIT_OK;
+  }
+  const LaunchFn l = find_pt(c->entry);
+  if (l == nullptr)
+    return fail(VIT_EUNSUPPORTED, "no parallel-traceback kernel compiled for K=%d beta=%d with these generators",
+                c->K, c->beta);
+  c->pt_f0 = f0;
+  c->pt_rule = rule;
+  c->pt_seed = seed;
+  c->pt_launch = l;
+  return VIT_OK;
+}
+
 void vit_destroy(vit_code* c) { delete c; }
 
 int64_t vit_llr_count(const vit_code* c, int64_t n) {
@@ -255,6 +307,13 @@ int64_t vit_output_bits(const vit_code* c, int64_t n) {
   if (c == nullptr || n < 0) return -1;
   if (c->mode == VIT_TERMINATED) return n > c->K - 1 ? n - (c->K - 1) : 0;
   return n;
+}
+
+// Subframes per tile of the parallel traceback (0 when it is off).
+static int64_t pt_subframes(const vit_code* c, int64_t n) {
+  if (c->pt_f0 <= 0) return 0;
+  const int64_t fb = tile_len(n, c->f);
+  return (fb + c->pt_f0 - 1) / c->pt_f0;
 }
 
 static size_t slab_task_words(const vit_code* c, int64_t n) {
@@ -271,6 +330,7 @@ size_t vit_decode_workspace(const vit_code* c, int64_t n) {
   const int64_t tasks = (tiles + tpt - 1) / tpt;
   size_t bytes = align_up((size_t)tasks * slab_task_words(c, n) * 4);
   if (c->period) bytes += align_up((size_t)n * c->beta);
+  bytes += align_up((size_t)(tiles * pt_subframes(c, n)));
   return bytes;
 }
 
@@ -303,6 +363,7 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "depuncture launch");
     dec_llr = dep;
+    p += align_up((size_t)n * c->beta);
   }
   KArgs a;
   memset(&a, 0, sizeof a);
@@ -321,7 +382,14 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
   a.slab = slab;
   a.task_words = (int64_t)tw;
   a.task_base = 0;
-  cudaError_t e = c->entry->launch(a, kWarpsPerCta, s);
+  if (c->pt_f0 > 0) {
+    a.pt_f0 = c->pt_f0;
+    a.pt_rule = c->pt_rule;
+    a.pt_seed = c->pt_seed;
+    a.pt_nsub = pt_subframes(c, n);
+    a.pt_states = p;
+  }
+  cudaError_t e = (c->pt_f0 > 0 ? c->pt_launch : c->entry->launch)(a, kWarpsPerCta, s);
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   return VIT_OK;
 }
@@ -381,6 +449,18 @@ int vit_encode(const vit_code* c, const uint8_t* bits, int64_t n, uint8_t* coded
   return VIT_OK;
 }
 
+int vit_hard_llr(const uint8_t* bits, int64_t count, int8_t* llr, vit_stream_t stream) {
+  if (count <= 0) return fail(VIT_EINVAL, "count must be >= 1");
+  if (bits == nullptr || llr == nullptr) return fail(VIT_EINVAL, "null device pointer");
+  const int64_t groups = (count + 7) / 8;
+  const unsigned grid = (unsigned)((groups + 255) / 256);
+  if ((groups + 255) / 256 > 0x7fffffffLL) return fail(VIT_EINVAL, "count too large");
+  hard_llr_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(bits, count, llr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "hard-decision expansion launch");
+  return VIT_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches
@@ -390,6 +470,11 @@ int vit_encode(const vit_code* c, const uint8_t* bits, int64_t n, uint8_t* coded
 struct vit_batch {
   struct Group {
     const CodeEntry* entry;
+    LaunchFn launch;  // the code's tile decoder, or its parallel-traceback variant
+    int64_t pt_f0 = 0, pt_nsub = 0;
+    int pt_rule = 0;
+    uint64_t pt_seed = 0;
+    uint8_t* d_pt = nullptr;
     Tiling tl;
     uint32_t M;
     int nframes;
@@ -407,6 +492,11 @@ struct vit_batch {
   };
   std::vector<Group> groups;
   std::vector<Dep> deps;
+  // one stream and completion event per group after the first: the groups
+  // run concurrently (fork/join with events, also inside a captured graph)
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
   std::vector<void*> allocs;
   int flags = 0;
   int warps = kWarpsPerCta;
@@ -440,6 +530,9 @@ void batch_free(vit_batch* b) {
   if (b == nullptr) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t x : b->side) cudaStreamDestroy(x);
+  for (cudaEvent_t x : b->done) cudaEventDestroy(x);
+  if (b->fork) cudaEventDestroy(b->fork);
   for (void* p : b->allocs) cudaFree(p);
   delete b;
 }
@@ -456,6 +549,11 @@ KArgs group_args(const vit_batch::Group& g) {
   a.ntasks = g.ntasks;
   a.slab = g.d_slab;
   a.task_words = g.task_words;
+  a.pt_f0 = g.pt_f0;
+  a.pt_rule = g.pt_rule;
+  a.pt_seed = g.pt_seed;
+  a.pt_nsub = g.pt_nsub;
+  a.pt_states = g.d_pt;
   return a;
 }
 
@@ -480,10 +578,18 @@ int batch_enqueue(vit_batch* b, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(e, "persistent decode launch");
     return VIT_OK;
   }
-  for (const auto& g : b->groups) {
-    cudaError_t e = g.entry->launch(group_args(g), b->warps, s);
-    if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");
+  // group 0 (the costliest) on the caller's stream, the others forked onto
+  // the plan's side streams and joined back before the batch completes
+  cudaError_t e = cudaSuccess;
+  if (b->groups.size() > 1) e = cudaEventRecord(b->fork, s);
+  for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; k++) {
+    e = cudaStreamWaitEvent(b->side[k - 1], b->fork, 0);
+    if (e == cudaSuccess) e = b->groups[k].launch(group_args(b->groups[k]), b->warps, b->side[k - 1]);
+    if (e == cudaSuccess) e = cudaEventRecord(b->done[k - 1], b->side[k - 1]);
   }
+  if (e == cudaSuccess) e = b->groups[0].launch(group_args(b->groups[0]), b->warps, s);
+  for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; k++) e = cudaStreamWaitEvent(s, b->done[k - 1], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");
   return VIT_OK;
 }
 }  // namespace
@@ -503,6 +609,7 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     if (f.mode == VIT_TERMINATED && f.n <= f.code->K - 1)
       return fail(VIT_EINVAL, "frame %d: terminated frame shorter than its tail", i);
   }
+  if (flags & ~(VIT_BATCH_GRAPH | VIT_BATCH_PERSISTENT | 0xff00)) return fail(VIT_EINVAL, "unknown batch flag");
   const int warps = (flags >> 8) & 0xff;
   if (warps != 0 && (warps < 1 || warps > 8)) return fail(VIT_EINVAL, "warps per CTA must be in [1, 8]");
   vit_batch* b = new (std::nothrow) vit_batch;
@@ -518,7 +625,9 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     int gi = -1;
     for (size_t k = 0; k < leaders.size(); k++) {
       const vit_code* l = leaders[k];
-      if (l->entry == c->entry && l->f == c->f && l->v1 == c->v1 && l->v2 == c->v2) gi = (int)k;
+      if (l->entry == c->entry && l->f == c->f && l->v1 == c->v1 && l->v2 == c->v2 && l->pt_f0 == c->pt_f0 &&
+          (c->pt_f0 == 0 || (l->pt_rule == c->pt_rule && l->pt_seed == c->pt_seed)))
+        gi = (int)k;
     }
     if (gi < 0) {
       leaders.push_back(c);
@@ -540,6 +649,10 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     const vit_code* c = leaders[k];
     vit_batch::Group g;
     g.entry = c->entry;
+    g.launch = c->pt_f0 > 0 ? c->pt_launch : c->entry->launch;
+    g.pt_f0 = c->pt_f0;
+    g.pt_rule = c->pt_rule;
+    g.pt_seed = c->pt_seed;
     g.tl = Tiling{c->f, c->v1, c->v2};
     g.M = (uint32_t)(2 * (c->K - 1) * 127 * c->beta + 1);
     g.nframes = (int)members[k].size();
@@ -574,6 +687,10 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
       tiles += nt;
       const int64_t w = max_window(c, f.n);
       if (w > maxw) maxw = w;
+      if (g.pt_f0 > 0) {
+        const int64_t ns = (tile_len(f.n, c->f) + g.pt_f0 - 1) / g.pt_f0;
+        if (ns > g.pt_nsub) g.pt_nsub = ns;
+      }
     }
     if (rc != VIT_OK) break;
     g.ntiles = tiles;
@@ -589,7 +706,8 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     g.d_frames = (Frame*)dalloc(sizeof(Frame) * g.nframes);
     g.d_tile0 = (int64_t*)dalloc(sizeof(int64_t) * g.nframes);
     g.d_slab = (uint32_t*)dalloc((size_t)g.ntasks * g.task_words * 4);
-    if (!g.d_frames || !g.d_tile0 || !g.d_slab) {
+    if (g.pt_f0 > 0) g.d_pt = (uint8_t*)dalloc((size_t)(g.ntiles * g.pt_nsub));
+    if (!g.d_frames || !g.d_tile0 || !g.d_slab || (g.pt_f0 > 0 && !g.d_pt)) {
       rc = fail(VIT_ENOMEM, "device allocation failed");
       break;
     }
@@ -601,9 +719,20 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     }
     b->groups.push_back(std::move(g));
   }
-  // two code groups with a compiled persistent kernel: one launch over a
-  // queue of all their tasks, longest windows first
-  if (rc == VIT_OK && b->groups.size() == 2) {
+  // costliest group first (it is launched on the caller's stream, first)
+  if (rc == VIT_OK) {
+    auto cost = [](const vit_batch::Group& g) {
+      int64_t c = 0;
+      for (int64_t L : g.task_len) c += L;
+      return (double)c * (double)(1 << (g.entry->K - 1));
+    };
+    std::stable_sort(b->groups.begin(), b->groups.end(),
+                     [&](const vit_batch::Group& x, const vit_batch::Group& y) { return cost(x) > cost(y); });
+  }
+  // with VIT_BATCH_PERSISTENT, two code groups with a compiled persistent
+  // kernel become one launch over a queue of all their tasks, longest first
+  if (rc == VIT_OK && (flags & VIT_BATCH_PERSISTENT) && b->groups.size() == 2 && b->groups[0].pt_f0 == 0 &&
+      b->groups[1].pt_f0 == 0) {
     bool swapped = false;
     const MixEntry* mx = find_mixed(b->groups[0].entry, b->groups[1].entry, &swapped);
     if (mx != nullptr) {
@@ -634,6 +763,18 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
         if (e != cudaSuccess) rc = cuda_fail(e, "queue upload");
       }
     }
+  }
+  if (rc == VIT_OK && b->mix == nullptr && b->groups.size() > 1) {
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; k++) {
+      cudaStream_t x = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+      if (e == cudaSuccess) b->side.push_back(x);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) b->done.push_back(ev);
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "group streams");
   }
   if (rc != VIT_OK) {
     batch_free(b);

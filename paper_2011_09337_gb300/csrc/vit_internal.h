@@ -24,6 +24,13 @@ struct KArgs {
   uint32_t* slab;        // survivor words, task_words per task
   int64_t task_words;
   int64_t task_base;     // first task index of this launch (for chunked launches)
+  // parallel traceback (pt_f0 > 0): subframe length, start rule, SplitMix64
+  // key, and one byte per subframe of every tile (pt_nsub per tile)
+  int64_t pt_f0;
+  int pt_rule;
+  uint64_t pt_seed;
+  uint8_t* pt_states;
+  int64_t pt_nsub;
 };
 
 VIT_HD int64_t find_frame(const int64_t* tile0, int nframes, int64_t gt) {
@@ -39,23 +46,29 @@ VIT_HD int64_t find_frame(const int64_t* tile0, int nframes, int64_t gt) {
 }
 
 #if defined(__CUDACC__)
-// Decodes warp task `task` of one code: 64 / G tiles, lanes grouped G per
-// tile pair.
-template <class C, bool kWords = true>
-__device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane) {
+// The lane's two tiles of warp task `task` (64 / G tiles per task, lanes
+// grouped G per tile pair), their end-aligned windows over Lw iterations,
+// the first iteration at which every window of the warp has started, and the
+// lane's survivor slab.  e1f: each tile's emitted end before clipping to the
+// frame's output count (global tile indices in gt).
+template <class C>
+__device__ __forceinline__ void task_setup(const KArgs& a, int64_t task, int lane, Half (&hw)[2], int64_t (&gt)[2],
+                                           int64_t (&e1f)[2], int& Lw, int& mu, Slab& sl) {
   constexpr int TPT = 64 / C::G;  // tiles per task
   const int pair = lane / C::G;
-  Half hw[2];
 #pragma unroll
   for (int h = 0; h < 2; h++) {
-    const int64_t gt = task * TPT + 2 * pair + h;
-    if (gt >= a.ntiles) {
+    gt[h] = task * TPT + 2 * pair + h;
+    e1f[h] = 0;
+    if (gt[h] >= a.ntiles) {
       hw[h] = idle_half();
-    } else if (a.frames == nullptr) {
-      hw[h] = make_half(a.f0, gt, a.tl);
     } else {
-      const int64_t fi = find_frame(a.tile0, a.nframes, gt);
-      hw[h] = make_half(a.frames[fi], gt - a.tile0[fi], a.tl);
+      const int64_t fi = (a.frames == nullptr) ? -1 : find_frame(a.tile0, a.nframes, gt[h]);
+      const Frame& fr = (fi < 0) ? a.f0 : a.frames[fi];
+      const int64_t b = (fi < 0) ? gt[h] : gt[h] - a.tile0[fi];
+      hw[h] = make_half(fr, b, a.tl);
+      const int64_t fb = tile_len(fr.n, a.tl.f);
+      e1f[h] = (b * fb + fb < fr.n) ? b * fb + fb : fr.n;
     }
   }
   int L = 1;
@@ -64,8 +77,8 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane)
     if (hw[h].active) L = max(L, (int)(hw[h].t1 - hw[h].t0));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) L = max(L, __shfl_xor_sync(0xffffffffu, L, o));
-  const int Lw = ((L + C::U - 1) / C::U) * C::U;
-  int mu = 0;
+  Lw = ((L + C::U - 1) / C::U) * C::U;
+  mu = 0;
 #pragma unroll
   for (int h = 0; h < 2; h++)
     if (hw[h].active) {
@@ -74,7 +87,17 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane)
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-  Slab sl{a.slab + task * a.task_words + lane * C::WORDS, 32 * C::WORDS};
+  sl = Slab{a.slab + task * a.task_words + lane * C::WORDS, 32 * C::WORDS};
+}
+
+// Decodes warp task `task` of one code.
+template <class C, bool kWords = true>
+__device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane) {
+  Half hw[2];
+  int64_t gt[2], e1f[2];
+  int Lw, mu;
+  Slab sl;
+  task_setup<C>(a, task, lane, hw, gt, e1f, Lw, mu, sl);
   // word loads need every active tile's groups to start on 4-byte boundaries
   bool aligned = true;
 #pragma unroll
@@ -95,7 +118,7 @@ __global__ void __maxnreg__(kMaxRegs) decode_tiles_kernel(const KArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t task = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (task >= a.ntasks) return;  // warp-uniform
-  run_task<C, (C::G == 1)>(a, task, lane);
+  run_task<C>(a, task, lane);
 }
 
 // Persistent kernel over the tasks of two codes: each warp takes the next
@@ -144,6 +167,7 @@ struct CodeEntry {
   int tiles_per_task;
   cudaError_t (*launch)(const KArgs&, int warps, cudaStream_t);
 };
+typedef cudaError_t (*LaunchFn)(const KArgs&, int warps, cudaStream_t);
 
 // A compiled persistent kernel for a pair of codes.
 struct MixEntry {
@@ -152,21 +176,27 @@ struct MixEntry {
 };
 
 #if defined(__CUDACC__)
-template <class C>
-cudaError_t launch_decode(const KArgs& a, int warps, cudaStream_t s) {
+// Launches `kernel` over the tasks of `a`, one warp per task (grid.x is
+// limited to 2^31-1 CTAs, so very large launches are split).
+template <void (*kernel)(const KArgs)>
+cudaError_t launch_tasks(const KArgs& a, int warps, cudaStream_t s) {
   if (warps < 1 || warps > 8) warps = kWarpsPerCta;
-  // grid.x is limited to 2^31-1 CTAs; split very large launches
   const int64_t maxc = (int64_t)1 << 30;
   for (int64_t t0 = 0; t0 < a.ntasks; t0 += maxc * warps) {
     KArgs b = a;
     b.task_base = t0;
     const int64_t tasks = (a.ntasks - t0 < maxc * warps) ? a.ntasks - t0 : maxc * warps;
     const unsigned grid = (unsigned)((tasks + warps - 1) / warps);
-    decode_tiles_kernel<C><<<grid, warps * 32, 0, s>>>(b);
+    kernel<<<grid, warps * 32, 0, s>>>(b);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+template <class C>
+cudaError_t launch_decode(const KArgs& a, int warps, cudaStream_t s) {
+  return launch_tasks<decode_tiles_kernel<C>>(a, warps, s);
 }
 
 template <class C0, class C1>
@@ -204,6 +234,9 @@ struct MixKey {
 };
 void register_mixed(const MixKey& a, const MixKey& b, cudaError_t (*launch)(const MixArgs&, int, cudaStream_t));
 const MixEntry* find_mixed(const CodeEntry* a, const CodeEntry* b, bool* swapped);
+// Tile decoders with the parallel traceback, registered by (K, beta, polys).
+void register_pt(const MixKey& k, LaunchFn launch);
+LaunchFn find_pt(const CodeEntry* e);
 
 }  // namespace vit
 
@@ -216,6 +249,10 @@ struct vit_code {
   int period;  // puncturing period (0 = none)
   uint8_t mask[4 * 64];
   const vit::CodeEntry* entry;
+  int64_t pt_f0;      // parallel traceback subframe length (0: serial traceback)
+  int pt_rule;        // VIT_PT_STORED or VIT_PT_RANDOM
+  uint64_t pt_seed;
+  vit::LaunchFn pt_launch;
 };
 
 namespace vit {

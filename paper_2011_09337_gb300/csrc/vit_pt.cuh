@@ -1,0 +1,176 @@
+// vit_pt.cuh -- tile decoding with the paper's first parallel traceback
+// (Sec. "Parallel Traceback Algorithm", Fig. pt1), for codes whose states
+// fit one lane (K <= 7).
+//
+// A tile's emitted stages [e0, e1) are cut into subframes of f0 stages.
+// Subframe k emits [s0, s1) = [e0 + k f0, min(e0 + (k+1) f0, e1)) and is
+// traced back from stage u = min(s1 + v2, t1) - 1 (it overlaps its right-hand
+// neighbour by v2 stages, whose bits it does not emit).  Its start state is
+// the tile's usual one (Alg. 2 argmax, or state 0 at the end of a terminated
+// frame) when u is the window's last stage; otherwise the argmax of stage u's
+// path metrics, recorded during the forward pass (rule 0), or the top K-1
+// bits of SplitMix64 output u under the caller's seed (rule 1).
+//
+// The forward pass is the tile decoder's (byte loads, both tiles of a lane
+// in the two 16-bit fields); after every stage at which a subframe of either
+// tile starts its traceback, the lane records that tile's argmax state.  The
+// traceback then runs per tile and per subframe.
+#pragma once
+#include "vit_acs.cuh"
+
+namespace vit {
+
+struct PtParams {
+  int64_t f0;     // subframe length (a multiple of 8)
+  int rule;       // 0: recorded argmax start, 1: SplitMix64 start
+  uint64_t seed;  // key of the SplitMix64 start
+};
+
+// Output i of SplitMix64 seeded with `seed` (Steele, Lea and Flood, OOPSLA
+// 2014): the generator adds 0x9E3779B97F4A7C15 to its state before each
+// output and returns the state mixed by two xor-shift-multiply rounds.
+VIT_HD uint64_t splitmix64_output(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Subframe k of a tile: emitted [s0, s1) and first traceback stage u.
+// e1f: the tile's emitted end before clipping to the frame's output count.
+struct Subframe {
+  int64_t s0, s1, u;
+};
+VIT_HD Subframe pt_subframe(const Half& h, int64_t e1f, int64_t f0, int64_t v2, int64_t k) {
+  Subframe s;
+  s.s0 = h.e0 + k * f0;
+  s.s1 = (s.s0 + f0 < e1f) ? s.s0 + f0 : e1f;
+  s.u = ((s.s1 + v2 < h.t1) ? s.s1 + v2 : h.t1) - 1;
+  return s;
+}
+
+// Argmax of tile h's field over the lane's states, ties to the lowest state.
+template <class C>
+VIT_HD int argmax_field(const uint32_t (&m)[C::NS], int h) {
+  uint32_t best = 0u;
+#pragma unroll
+  for (int q = 0; q < C::NS; q++) {
+    const uint32_t key = (((m[q] >> (16 * h)) & 0xffffu) << 8) | (uint32_t)(255 - q);
+    best = key > best ? key : best;
+  }
+  return 255 - (int)(best & 0xffu);
+}
+
+// Records the argmax of every subframe of tile h whose traceback starts at
+// iteration i (next[h]: the next such iteration, k[h]: its subframe).
+template <class C>
+VIT_HD void pt_capture(const uint32_t (&m)[C::NS], int i, const Half (&hw)[2], const int64_t (&e1f)[2],
+                       const int64_t (&nsub)[2], int64_t v2, const PtParams& pt, uint8_t* const (&st)[2],
+                       int (&next)[2], int64_t (&k)[2]) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    if (next[h] != i) continue;
+    const int best = argmax_field<C>(m, h);
+    while (k[h] < nsub[h]) {
+      const Subframe sf = pt_subframe(hw[h], e1f[h], pt.f0, v2, k[h]);
+      const int it = hw[h].start + (int)(sf.u - hw[h].t0);
+      if (it > i) {
+        next[h] = it;
+        break;
+      }
+      if (it == i) st[h][k[h]] = (uint8_t)best;  // (it < i: a SplitMix64 start)
+      k[h]++;
+    }
+    if (k[h] >= nsub[h]) next[h] = -1;
+  }
+}
+
+// First capture iteration of tile h (-1: none).  With rule 1 only the
+// subframes traced from the window's last stage need their argmax, which the
+// capture after the last stage records.
+VIT_HD int pt_first_capture(const Half& h, int64_t e1f, int64_t nsub, int64_t v2, const PtParams& pt, int Lw) {
+  if (!h.active || nsub <= 0) return -1;
+  if (pt.rule != 0) return Lw - 1;
+  const Subframe sf = pt_subframe(h, e1f, pt.f0, v2, 0);
+  return h.start + (int)(sf.u - h.t0);
+}
+
+// Traceback of tile h, one subframe at a time (last first).
+template <class C>
+VIT_HD void pt_traceback(const Half& hw, int h, int64_t e1f, int64_t nsub, int64_t v2, const PtParams& pt,
+                         const uint8_t* st, Slab sl) {
+  for (int64_t k = nsub - 1; k >= 0; k--) {
+    const Subframe sf = pt_subframe(hw, e1f, pt.f0, v2, k);
+    if (k > 0) {  // the next subframe's survivor words, into L2
+      const Subframe nf = pt_subframe(hw, e1f, pt.f0, v2, k - 1);
+      slab_prefetch_l2(sl, hw.start + (int)(nf.s0 - hw.t0), (int)(nf.u - nf.s0 + 1));
+    }
+    uint32_t j;
+    if (sf.u == hw.t1 - 1)
+      j = hw.end_zero ? 0u : (uint32_t)st[k];
+    else if (pt.rule == 0)
+      j = (uint32_t)st[k];
+    else
+      j = (uint32_t)(splitmix64_output(pt.seed, (uint64_t)sf.u) >> (64 - C::KM1));
+    const int64_t emit_hi = sf.s1 < hw.e1 ? sf.s1 : hw.e1;
+    uint32_t acc = 0u;
+    for (int64_t t = sf.u; t >= sf.s0; t--) {
+      uint32_t w[C::WORDS];
+      load_words<C>(sl, hw.start + (int)(t - hw.t0), w);
+      const uint32_t d = tb_decision<C>(w, j, h);
+      if (t < emit_hi) {
+        acc |= ((j >> (C::K - 2)) & 1u) << (t & 7);
+        if ((t & 7) == 0 || t == sf.s0) {
+          store_byte(hw.out + (t >> 3), acc);
+          acc = 0u;
+        }
+      }
+      j = (2u * j + d) & (uint32_t)(C::S - 1);
+    }
+  }
+}
+
+// Decodes the two tiles of one lane with the parallel traceback.  st[h]:
+// the tile's recorded start states (one byte per subframe).
+template <class C>
+VIT_HD void decode_pair_pt(const Half (&hw)[2], const int64_t (&e1f)[2], int Lw, int masked_until, uint32_t M,
+                           Slab sl, int64_t v2, const PtParams& pt, uint8_t* const (&st)[2]) {
+  static_assert(C::G == 1 && C::U == 2, "one lane per tile pair");
+  uint32_t ma[C::NS], mb[C::NS];
+#pragma unroll
+  for (int s = 0; s < C::NS; s++) ma[s] = 0x80008000u;
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+    if (hw[h].known && hw[h].start == 0) init_half<C>(ma, h, true, M);
+  int64_t nsub[2], k[2] = {0, 0};
+  int next[2];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    nsub[h] = hw[h].active && e1f[h] > hw[h].e0 ? (e1f[h] - hw[h].e0 + pt.f0 - 1) / pt.f0 : 0;
+    next[h] = pt_first_capture(hw[h], e1f[h], nsub[h], v2, pt, Lw);
+  }
+  const int ngroups = Lw / C::U;
+  LlrGroup<C> cur, nxt;
+  load_group<C>(hw, 0, cur);
+  for (int g = 0; g < ngroups; g++) {
+    const int i0 = g * C::U;
+    if (g + 1 < ngroups) {
+      if (i0 + C::U < masked_until)
+        load_group<C>(hw, i0 + C::U, nxt);
+      else
+        load_group_fast<C>(hw, i0 + C::U, nxt);
+    }
+    const bool masked = i0 < masked_until;
+    fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl);
+    if (next[0] == i0 || next[1] == i0) pt_capture<C>(mb, i0, hw, e1f, nsub, v2, pt, st, next, k);
+    fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl);
+    if (next[0] == i0 + 1 || next[1] == i0 + 1) pt_capture<C>(ma, i0 + 1, hw, e1f, nsub, v2, pt, st, next, k);
+    if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
+    cur = nxt;
+  }
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+    if (hw[h].active) pt_traceback<C>(hw[h], h, e1f[h], nsub[h], v2, pt, st[h], sl);
+}
+
+}  // namespace vit

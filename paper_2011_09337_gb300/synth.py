@@ -27,6 +27,8 @@ CODE_K7_R12 = (7, 2, (0o171, 0o133))
 CODE_K7_R13 = (7, 3, (0o133, 0o171, 0o165))
 CODE_K9_R12 = (9, 2, (0o561, 0o753))
 PUNCT_R34 = np.array([[1, 1, 0], [1, 0, 1]], dtype=np.uint8)  # rows: coded stream, cols: stage mod 3
+PUNCT_R23 = np.array([[1, 1], [1, 0]], dtype=np.uint8)
+PUNCT_R56 = np.array([[1, 1, 0, 1, 0], [1, 0, 1, 0, 1]], dtype=np.uint8)
 
 Encoder = Callable[[np.ndarray], np.ndarray]  # bits (n,) -> coded bits (n, beta)
 

@@ -16,7 +16,8 @@ import torch
 from . import build_lib
 
 STREAM, TERMINATED, FREE_START = 0, 1, 2
-BATCH_GRAPH, BATCH_TUNE = 1, 2
+BATCH_GRAPH, BATCH_PERSISTENT = 1, 4
+PT_STORED, PT_RANDOM = 0, 1
 
 _lib = None
 
@@ -54,6 +55,8 @@ def load(path: str | None = None):
         "vit_encode": (i32, [vp, vp, i64, vp, vp]),
         "vit_last_error": (ctypes.c_char_p, []),
         "vit_code_supported": (i32, [i32, i32, vp]),
+        "vit_set_parallel_traceback": (i32, [vp, i64, i32, ctypes.c_uint64]),
+        "vit_hard_llr": (i32, [vp, i64, vp, vp]),
     }
     optional = {
         "vit_batch_plan": (i32, [ctypes.POINTER(vp), vp, i32, i32]),
@@ -95,7 +98,10 @@ class Code:
 
     def __init__(self, K: int, beta: int, polys: Sequence[int], f: int = 0, v: int = 0,
                  v1: int | None = None, v2: int | None = None, mode: int = STREAM,
-                 puncture: Sequence[Sequence[int]] | None = None):
+                 puncture: Sequence[Sequence[int]] | None = None, pt_f0: int = 0, pt_rule: int = 0,
+                 pt_seed: int = 0):
+        """pt_f0 > 0 selects the parallel traceback with subframes of pt_f0
+        stages (pt_rule: PT_STORED or PT_RANDOM, pt_seed: SplitMix64 key)."""
         L = load()
         self.K, self.beta, self.polys = K, beta, tuple(int(p) for p in polys)
         self.f = f
@@ -117,6 +123,9 @@ class Code:
                 raise ValueError("puncturing mask must be beta x period")
             self.puncture = m
             _check(L.vit_set_puncture(h, m.ctypes.data_as(ctypes.c_void_p), m.shape[1]))
+        self.pt = (pt_f0, pt_rule, pt_seed)
+        if pt_f0:
+            _check(L.vit_set_parallel_traceback(h, pt_f0, pt_rule, pt_seed))
 
     @property
     def handle(self):
@@ -177,6 +186,18 @@ def encode(code: Code, bits: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def hard_llr(bits: torch.Tensor, count: int) -> torch.Tensor:
+    """Hard-decision input: packed received bits (uint8 CUDA tensor, LSB-first)
+    -> int8 LLRs of +1 (bit 0) / -1 (bit 1), ``count`` of them."""
+    if not (bits.is_cuda and bits.dtype == torch.uint8 and bits.is_contiguous()):
+        raise ValueError("bits must be a contiguous uint8 CUDA tensor")
+    if bits.numel() * 8 < count:
+        raise ValueError("fewer packed bits than count")
+    out = torch.empty(count, dtype=torch.int8, device=bits.device)
+    _check(load().vit_hard_llr(bits.data_ptr(), count, out.data_ptr(), _stream(bits.device)))
+    return out
+
+
 class _Frame(ctypes.Structure):
     _fields_ = [("code", ctypes.c_void_p), ("llr", ctypes.c_void_p), ("n", ctypes.c_int64),
                 ("mode", ctypes.c_int), ("bits_out", ctypes.c_void_p)]
@@ -185,9 +206,11 @@ class _Frame(ctypes.Structure):
 class Batch:
     """A planned batch of frames (vit_batch_plan): decodes the same device
     buffers every time ``run()`` is called; ``graph=True`` replays one
-    captured CUDA graph."""
+    captured CUDA graph.  Code groups run as concurrent launches, or with
+    ``persistent=True`` (two groups with a compiled two-code kernel) as one
+    persistent launch over a shared task queue."""
 
-    def __init__(self, frames, graph: bool = True, warps: int = 0):
+    def __init__(self, frames, graph: bool = True, warps: int = 0, persistent: bool = False):
         """frames: iterable of (code, llr, n, mode, out) with CUDA tensors;
         warps: CTA size in warps (1..8, 0 = library default)."""
         L = load()
@@ -204,7 +227,7 @@ class Batch:
             arr[i] = _Frame(code.handle.value, llr.data_ptr(), n, mode, out.data_ptr())
             self._keep.append((code, llr, out))
         h = ctypes.c_void_p()
-        flags = (BATCH_GRAPH if graph else 0) | ((int(warps) & 0xFF) << 8)
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_PERSISTENT if persistent else 0) | ((int(warps) & 0xFF) << 8)
         _check(L.vit_batch_plan(ctypes.byref(h), arr, len(frames), flags))
         self._h = h
         self.device = frames[0][1].device

@@ -111,3 +111,48 @@ def test_decode_rejects_bad_arguments_before_any_launch(lib):
     assert b"workspace too small" in lib.vit_last_error()
     assert lib.vit_decode_ws(None, fake, 100, fake, fake, 1 << 30, None) == -1
     lib.vit_destroy(h)
+
+
+class _VitFrame(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("llr", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("mode", ctypes.c_int), ("bits_out", ctypes.c_void_p)]
+
+
+def test_batch_plan_rejects_bad_arguments_before_any_device_call(lib):
+    rc, h = _create(lib, 7, 2, (0o171, 0o133), 1024, 48)
+    assert rc == 0
+    plan = lib.vit_batch_plan
+    plan.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    out = ctypes.c_void_p()
+    fake = 0x1000  # never dereferenced: every check below fails first
+    frames = (_VitFrame * 2)(_VitFrame(h.value, fake, 5000, 0, fake), _VitFrame(h.value, fake, 70, 1, fake))
+    for flags, msg in ((2, b"flag"), (1 << 16, b"flag"), (9 << 8, b"warps")):
+        assert plan(ctypes.byref(out), ctypes.cast(frames, ctypes.c_void_p), 2, flags) == -1
+        assert msg in lib.vit_last_error() and not out.value
+    bad = (_VitFrame * 1)(_VitFrame(h.value, fake, 5000, 7, fake))
+    assert plan(ctypes.byref(out), ctypes.cast(bad, ctypes.c_void_p), 1, 1) == -1
+    assert b"mode" in lib.vit_last_error()
+    short = (_VitFrame * 1)(_VitFrame(h.value, fake, 6, 1, fake))
+    assert plan(ctypes.byref(out), ctypes.cast(short, ctypes.c_void_p), 1, 1) == -1
+    assert plan(ctypes.byref(out), ctypes.cast(frames, ctypes.c_void_p), 0, 1) == -1
+    lib.vit_destroy(h)
+
+
+def test_parallel_traceback_setter_checks(lib):
+    f = lib.vit_set_parallel_traceback
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64]
+    rc, h = _create(lib, 7, 2, (0o171, 0o133), 1024, 48)
+    assert rc == 0
+    assert f(h, 32, 0, 0) == 0 and f(h, 0, 0, 0) == 0 and f(h, 64, 1, 2**64 - 1) == 0
+    for f0, rule in ((12, 0), (-8, 0), (32, 2)):
+        assert f(h, f0, rule, 0) == -1 and lib.vit_last_error()
+    # the parallel traceback adds one byte per subframe of every tile to the scratch
+    f(h, 0, 0, 0)
+    base = lib.vit_decode_workspace(h, 1 << 20)
+    f(h, 32, 0, 0)
+    assert lib.vit_decode_workspace(h, 1 << 20) - base >= 1024 * 32
+    lib.vit_destroy(h)
+    rc, h = _create(lib, 9, 2, (0o561, 0o753), 2048, 96)
+    assert rc == 0
+    assert f(h, 32, 0, 0) == -2 and b"parallel-traceback" in lib.vit_last_error()
+    lib.vit_destroy(h)

@@ -1,6 +1,7 @@
 """Batched decoding (vit_batch_plan / vit_batch_run) against the oracle:
-mixed codes and uneven frame lengths in one persistent launch, graph replay,
-CTA sizes, and agreement with per-frame launches."""
+mixed codes and uneven frame lengths as concurrent per-code launches or one
+persistent launch, graph replay, CTA sizes, and agreement with per-frame
+launches."""
 import numpy as np
 import pytest
 import torch
@@ -45,10 +46,10 @@ def test_mixed_codes_one_launch(vit, tiling):
         ins.append(x)
         outs.append(o)
         specs.append((c, x, n, vit.TERMINATED, o))
-    for warps in (4, 1, 8):
+    for warps, persistent in ((4, False), (1, False), (8, False), (4, True), (2, True)):
         for o in outs:
             o.fill_(0xAA)
-        b = vit.Batch(specs, graph=True, warps=warps)
+        b = vit.Batch(specs, graph=True, warps=warps, persistent=persistent)
         b.run()
         b.run()  # replay of the captured graph
         torch.cuda.synchronize()
@@ -57,7 +58,8 @@ def test_mixed_codes_one_launch(vit, tiling):
             f, v = tiling[ci]
             want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v, oracle.TERMINATED)[: n - (K - 1)]
             got = synth.unpack_bits(outs[k].cpu().numpy(), n - (K - 1))
-            np.testing.assert_array_equal(got, want, err_msg=f"frame {k} code {ci} n={n} warps={warps}")
+            np.testing.assert_array_equal(got, want, err_msg=f"frame {k} code {ci} n={n} warps={warps} "
+                                                             f"persistent={persistent}")
     # per-frame launches give the same bits
     for k, (ci, n, s) in enumerate(frames[:20]):
         one = vit.decode(cobj[ci], ins[k], n)

@@ -107,6 +107,29 @@ def test_punctured_rate_three_quarters(vit):
         np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("key", ["k7", "k9", "k7r13", "k5"])
+@pytest.mark.parametrize("mask_name", ["PUNCT_R23", "PUNCT_R34", "PUNCT_R56", "drop_third"])
+def test_arbitrary_puncturing_masks(vit, key, mask_name):
+    """Rate 2/3, 3/4, 5/6 and a mask that removes every third coded bit of a
+    rate-1/3 code, for K = 5, 7, 9; each decoded like the oracle's
+    de-punctured stream (phase by global stage index, any f and v)."""
+    K, beta, polys = CODES[key]
+    if mask_name == "drop_third":
+        mask = np.ones((beta, 3), np.uint8)
+        mask[beta - 1, 1] = 0
+        mask[0, 2] = 0
+    else:
+        mask = getattr(synth, mask_name)
+        if mask.shape[0] != beta:
+            pytest.skip("mask for rate-1/2 codes")
+    for n, f, v in ((20000, 2048, 8 * (K - 1)), (3001, 256, 10), (1500, 0, 0)):
+        s = synth.make_stream(_enc(CODES[key]), beta, n, 5.0, seed=n + K, mask=mask)
+        dep = oracle.depuncture(s.llr, n, beta, mask)
+        want = oracle.viterbi_blocked(K, beta, polys, dep, f, v, v)
+        got = _gpu_decode(vit, CODES[key], s.llr, f, v, oracle.STREAM, n, puncture=mask)
+        np.testing.assert_array_equal(got, want, err_msg=f"n={n} f={f} v={v}")
+
+
 def test_config0_terminated_frame(vit):
     # one zero-terminated frame of 4096 info bits + 6 tail bits, Eb/N0 3 dB, full-frame decode
     K, beta, polys = CODES["k7"]
@@ -164,3 +187,21 @@ def test_config4_k7_punctured_sampled(vit):
         want = oracle.viterbi_blocked(K, beta, polys, dep, 2048, 64, 64, blocks=(int(b), int(b) + 1))
         np.testing.assert_array_equal(got[b * 2048:(b + 1) * 2048], want[b * 2048:(b + 1) * 2048],
                                       err_msg=f"tile {b}")
+
+
+@pytest.mark.parametrize("key", ["k7", "k9", "k7r13"])
+def test_hard_decision_input(vit, key):
+    """vit_hard_llr expands packed received bits to +-1 LLRs; decoding them
+    matches the oracle on the same +-1 LLRs (stream and punctured)."""
+    K, beta, polys = CODES[key]
+    for n, f, v, mask in ((50_000, 1024, 48, None), (7001, 256, 30, synth.PUNCT_R34 if beta == 2 else None)):
+        s = synth.make_stream(_enc(CODES[key]), beta, n, 5.0, seed=n + K, mask=mask, quantize=False)
+        rx = (s.llr.reshape(-1) < 0).astype(np.uint8)  # hard decisions of the kept symbols
+        packed = torch.from_numpy(synth.pack_bits(rx)).cuda()
+        llr = vit.hard_llr(packed, rx.size)
+        np.testing.assert_array_equal(llr.cpu().numpy(), np.where(rx == 1, -1, 1).astype(np.int8))
+        code = vit.Code(K, beta, polys, f=f, v=v, puncture=mask)
+        got = synth.unpack_bits(vit.decode(code, llr, n).cpu().numpy(), n)
+        pm = np.where(rx == 1, -1, 1).astype(np.int8)
+        dep = pm.reshape(n, beta) if mask is None else oracle.depuncture(pm, n, beta, mask)
+        np.testing.assert_array_equal(got, oracle.viterbi_blocked(K, beta, polys, dep, f, v, v))

@@ -297,17 +297,22 @@ def test_punctured_noiseless_recovery_and_free_distance():
     # Textbook pin: the IEEE 802.11a assignment (row [110] on generator 133,
     # row [101] on generator 171) has free distance 5.  The workload's literal
     # row order ([110] on 171, [101] on 133) gives 4.
-    def dfree(pol):
+    def dfree(pol, mask=synth.PUNCT_R34):
+        P = mask.shape[1]
         best = 99
         for m in range(1, 1 << 12):
             msg = np.array([(m >> t) & 1 for t in range(12)] + [0] * (K - 1), dtype=np.uint8)
             cm = oracle.encode(K, beta, pol, msg)
-            for ph in range(3):
-                keep = synth.PUNCT_R34.astype(bool)[:, (np.arange(cm.shape[0]) + ph) % 3].T
+            for ph in range(P):
+                keep = mask.astype(bool)[:, (np.arange(cm.shape[0]) + ph) % P].T
                 best = min(best, int(cm[keep].sum()))
         return best
     assert dfree((0o133, 0o171)) == 5
     assert dfree((0o171, 0o133)) == 4
+    # the IEEE 802.11 rate-2/3 and rate-5/6 patterns on (133, 171): free
+    # distances 6 and 4 (textbook values for these punctured codes)
+    assert dfree((0o133, 0o171), synth.PUNCT_R23) == 6
+    assert dfree((0o133, 0o171), synth.PUNCT_R56) == 4
 
 
 # ------------------------------------------------------- path-metric forms
@@ -397,3 +402,45 @@ def test_punctured_stream_noise_uses_the_punctured_rate():
     s = synth.make_stream(lambda x: np.zeros((x.size, 2), np.uint8), 2, 3000, 4.0, seed=1, mask=mask)
     assert s.sigma ** 2 == pytest.approx(1 / (2 * 0.75 * 10 ** 0.4))
     assert s.llr.size == synth.kept_symbols(3000, mask) == 4000
+
+
+# ------------------------------------------------------ hard-decision input
+def test_hard_decision_is_minimum_hamming_distance_decoding():
+    """+-1 LLRs from received bits: the full-frame decoder returns a message
+    whose codeword is at minimum Hamming distance from the received bits
+    (exhaustive search over all 2^10 terminated messages)."""
+    for key in ("k3", "k5", "k7"):
+        K, beta, polys = CODES[key]
+        g = synth.rng(40 + K)
+        n_info = 10
+        msgs = np.array([[(m >> t) & 1 for t in range(n_info)] + [0] * (K - 1) for m in range(1 << n_info)],
+                        dtype=np.uint8)
+        words = np.stack([oracle.encode(K, beta, polys, m) for m in msgs])  # (2^10, n, beta)
+        for trial in range(6):
+            rx = words[g.integers(0, 1 << n_info)].copy()
+            flips = g.random(rx.shape) < 0.12
+            rx ^= flips.astype(np.uint8)
+            llr = np.where(rx == 1, -1, 1).astype(np.int8)
+            bits, _ = oracle.viterbi_full(K, beta, polys, llr, oracle.TERMINATED)
+            dist = (words != rx[None]).reshape(len(msgs), -1).sum(axis=1)
+            got = oracle.encode(K, beta, polys, bits)
+            assert int((got != rx).sum()) == int(dist.min())
+
+
+def test_soft_decision_gain_of_about_two_db():
+    """Sec. "Hard-decision vs. Soft-decision": soft decisions lower the BER by
+    about 2.3 dB.  Fixed seeds, K=7 (171,133), f=1024, v=48: the hard-input
+    BER at x + 1.5 dB is still above the soft BER at x, and at x + 3 dB below
+    it (x = 3 dB)."""
+    K, beta, polys = CODES["k7"]
+    n = 120_000
+
+    def ber(ebn0, hard):
+        s = synth.make_stream(lambda x: oracle.encode(K, beta, polys, x), beta, n, ebn0, seed=3, quantize=False)
+        llr = np.where(s.llr < 0, -1, 1).astype(np.int8) if hard else synth.quantize_llr(s.llr)
+        return float(np.mean(oracle.viterbi_blocked(K, beta, polys, llr, 1024, 48, 48) != s.bits))
+
+    soft3 = ber(3.0, False)
+    assert 0 < soft3 < 2e-3
+    assert ber(4.5, True) > soft3
+    assert ber(6.0, True) < soft3
