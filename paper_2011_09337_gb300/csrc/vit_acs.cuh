@@ -524,27 +524,6 @@ VIT_HD void fwd_stage_words(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], int i,
   store_words(sl.base + (int64_t)i * sl.stride, wd, C::WORDS);
 }
 
-// Traceback step (Alg. 2) of both tiles at iteration i.
-template <class C>
-VIT_HD void tb_stage(int i, const uint32_t (&w)[C::WORDS], int (&s)[2], uint32_t (&acc)[2], const Half (&hw)[2]) {
-#pragma unroll
-  for (int h = 0; h < 2; h++) {
-    const int64_t t = hw[h].t0 + (int64_t)(i - hw[h].start);
-    const int j = s[h];
-    const uint32_t word = pick_word<C>(w, j);
-    const uint32_t d = ((word >> (16 * h + surv_pos<C>(j))) & 1u) ^ (h == 0 ? 1u : 0u);
-    const uint32_t bit = (uint32_t)(j >> (C::K - 2)) & 1u;
-    s[h] = ((j << 1) | (int)d) & (C::S - 1);
-    if (hw[h].active && t >= hw[h].e0 && t < hw[h].e1) {
-      acc[h] |= bit << (t & 7);
-      if ((t & 7) == 0 || t == hw[h].e0) {
-        hw[h].out[t >> 3] = (uint8_t)acc[h];
-        acc[h] = 0;
-      }
-    }
-  }
-}
-
 // x >> (n mod 32) (funnel shift of x with itself; only the low 5 bits of n
 // are used).
 VIT_HD uint32_t rotr32(uint32_t x, uint32_t n) {
@@ -594,28 +573,24 @@ VIT_HD void slab_prefetch_l2(const Slab& sl, int i, int cnt) {
 #endif
 }
 
-// Traceback (Alg. 2) of two tiles whose windows share their offsets and
-// emit whole bytes: r0/r1 are the first/one-past-last emitted iterations,
-// r1 - r0 a multiple of 8 and r1 + K - 1 <= Lw.  Following a decision d at
+// Traceback (Alg. 2) of the two tiles of a lane.  Following a decision d at
 // iteration i gives state (2j + d) mod S, whose bit K-2 after K-1 further
-// steps is d: d is the decoded bit of iteration i - (K-1).  So iterations
-// [r0 + K-1, Lw) are read and each aligned group of 8 emits one byte per tile.
-// Survivor words come from HBM: L2 prefetches run 4 groups ahead and three
-// register buffers hold the current group and the next two.
+// steps is d: d is the decoded bit of iteration i - (K-1).  Keeping
+// j = 2j + d unmasked therefore leaves the decoded bits of the iterations
+// x, x+1, ... in bits 0, 1, ... of j once iteration x + K - 1 is read, and
+// the start state's own K-1 bits stand for the top K-1 iterations (as if
+// read at iterations Lw .. Lw + K - 2).  Tile h emits iterations
+// [r0[h], r1[h]) (r0 at an output byte boundary); its bytes are taken from j
+// at checkpoints every 8 iterations, highest byte first, the partial last
+// byte masked.  Survivor words: three register buffers of 8 stages, loads
+// issued two groups ahead.
 template <class C>
-struct TbState {
-  uint32_t j0, j1, acc0, acc1;
-};
-
-template <class C>
-VIT_HD void tb_group(TbState<C>& st, const uint32_t (&w)[8][C::WORDS]) {
+VIT_HD void tb_group(uint32_t& j0, uint32_t& j1, const uint32_t (&w)[8][C::WORDS]) {
 #pragma unroll
   for (int k = 7; k >= 0; k--) {
-    const uint32_t d0 = tb_decision<C>(w[k], st.j0, 0), d1 = tb_decision<C>(w[k], st.j1, 1);
-    st.j0 = 2u * st.j0 + d0;
-    st.j1 = 2u * st.j1 + d1;
-    st.acc0 = 2u * st.acc0 + d0;
-    st.acc1 = 2u * st.acc1 + d1;
+    const uint32_t d0 = tb_decision<C>(w[k], j0, 0), d1 = tb_decision<C>(w[k], j1, 1);
+    j0 = 2u * j0 + d0;
+    j1 = 2u * j1 + d1;
   }
 }
 
@@ -625,49 +600,69 @@ VIT_HD void tb_load_group(const Slab& sl, int i, uint32_t (&w)[8][C::WORDS]) {
   for (int k = 0; k < 8; k++) load_words<C>(sl, i + k, w[k]);
 }
 
+// Emits the bytes of one tile whose lowest output iteration is at least x
+// (j holds the outputs from x upward); nb: next byte to emit, descending.
+VIT_HD void tb_emit(uint32_t j, int x, int r0, int r1, int& nb, uint8_t* out) {
+  int sh = r0 + 8 * nb - x;
+  while (nb >= 0 && sh >= 0) {
+    const int left = r1 - r0 - 8 * nb;
+    const uint32_t mask = left >= 8 ? 0xffu : ((1u << left) - 1u);
+    store_byte(out + nb, (j >> sh) & mask);
+    nb--;
+    sh -= 8;
+  }
+}
+
 template <class C>
-VIT_HD void traceback_bytes(const Half (&hw)[2], int Lw, int r0, int r1, const int (&s0)[2], Slab sl) {
-  const int ib = r0 + C::KM1;
-  const int nbytes = (r1 - r0) >> 3;
-  TbState<C> st{(uint32_t)s0[0], (uint32_t)s0[1], 0u, 0u};
-  // the partial group above the last whole group of 8 (no emission there)
+VIT_HD void traceback_pair(const Half (&hw)[2], int Lw, const int (&s0)[2], Slab sl) {
+  bool act[2];
+  int r0[2], r1[2], nb[2];
+  uint8_t* o[2];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    act[h] = hw[h].active && hw[h].e1 > hw[h].e0;
+    r0[h] = hw[h].start + (int)(hw[h].e0 - hw[h].t0);
+    r1[h] = hw[h].start + (int)(hw[h].e1 - hw[h].t0);
+    nb[h] = act[h] ? (r1[h] - r0[h] + 7) / 8 - 1 : -1;
+    o[h] = hw[h].out + (hw[h].e0 >> 3);
+  }
+  if (!act[0] && !act[1]) return;
+  const int rmin = act[0] ? (act[1] && r0[1] < r0[0] ? r0[1] : r0[0]) : r0[1];
+  const int ib = rmin + C::KM1;  // lowest iteration read
+  uint32_t j0 = (uint32_t)s0[0], j1 = (uint32_t)s0[1];
+  auto checkpoint = [&](int x) {
+    tb_emit(j0, x, r0[0], r1[0], nb[0], o[0]);
+    tb_emit(j1, x, r0[1], r1[1], nb[1], o[1]);
+  };
+  checkpoint(Lw - C::KM1);  // bytes made of start-state bits only
+  if (ib >= Lw) return;
+  // the partial group below Lw above the last whole group of 8
   const int top = ib + 8 * ((Lw - ib) >> 3);
-  int q = ((top - ib) >> 3) - 1;  // highest whole group
-  slab_prefetch_l2(sl, ib + 8 * (q - 3 > 0 ? q - 3 : 0), 8 * (q + 1 < 4 ? q + 1 : 4));
   for (int i = Lw - 1; i >= top; i--) {
     uint32_t w[C::WORDS];
     load_words<C>(sl, i, w);
-    st.j0 = 2u * st.j0 + tb_decision<C>(w, st.j0, 0);
-    st.j1 = 2u * st.j1 + tb_decision<C>(w, st.j1, 1);
+    j0 = 2u * j0 + tb_decision<C>(w, j0, 0);
+    j1 = 2u * j1 + tb_decision<C>(w, j1, 1);
   }
+  if (top < Lw) checkpoint(top - C::KM1);
+  int q = ((top - ib) >> 3) - 1;  // highest whole group
   if (q < 0) return;
-  uint8_t* o0 = hw[0].out + (hw[0].e0 >> 3);
-  uint8_t* o1 = hw[1].out + (hw[1].e0 >> 3);
-  auto emit = [&](int g) {
-    if (g < nbytes) {
-      store_byte(o0 + g, st.acc0 & 0xffu);
-      store_byte(o1 + g, st.acc1 & 0xffu);
-    }
-  };
   uint32_t b0[8][C::WORDS], b1[8][C::WORDS], b2[8][C::WORDS];
   tb_load_group<C>(sl, ib + 8 * q, b0);
   if (q >= 1) tb_load_group<C>(sl, ib + 8 * (q - 1), b1);
   // invariant at the loop top: b0 holds group q, b1 group q-1 (if q >= 1)
   while (true) {
-    if (q >= 4) slab_prefetch_l2(sl, ib + 8 * (q - 4), 8);
     if (q >= 2) tb_load_group<C>(sl, ib + 8 * (q - 2), b2);
-    tb_group<C>(st, b0);
-    emit(q);
+    tb_group<C>(j0, j1, b0);
+    checkpoint(rmin + 8 * q);
     if (--q < 0) break;
-    if (q >= 4) slab_prefetch_l2(sl, ib + 8 * (q - 4), 8);
     if (q >= 2) tb_load_group<C>(sl, ib + 8 * (q - 2), b0);
-    tb_group<C>(st, b1);
-    emit(q);
+    tb_group<C>(j0, j1, b1);
+    checkpoint(rmin + 8 * q);
     if (--q < 0) break;
-    if (q >= 4) slab_prefetch_l2(sl, ib + 8 * (q - 4), 8);
     if (q >= 2) tb_load_group<C>(sl, ib + 8 * (q - 2), b1);
-    tb_group<C>(st, b2);
-    emit(q);
+    tb_group<C>(j0, j1, b2);
+    checkpoint(rmin + 8 * q);
     if (--q < 0) break;
     // b0 holds group q, b1 group q-1: the invariant again
   }
@@ -752,52 +747,7 @@ VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t 
     s[h] = hw[h].end_zero ? 0 : best;
   }
 
-  {
-    const int r0 = hw[0].start + (int)(hw[0].e0 - hw[0].t0);
-    const int r1 = hw[0].start + (int)(hw[0].e1 - hw[0].t0);
-    const bool same = hw[0].active && hw[1].active && hw[0].start == hw[1].start &&
-                      hw[0].e0 - hw[0].t0 == hw[1].e0 - hw[1].t0 && hw[0].e1 - hw[0].t0 == hw[1].e1 - hw[1].t0;
-    if (same && r1 > r0 && ((r1 - r0) & 7) == 0 && r1 + C::KM1 <= Lw) {
-      traceback_bytes<C>(hw, Lw, r0, r1, s, sl);
-      return;
-    }
-  }
-
-  // lowest iteration that still emits a bit, over both tiles
-  int stop = Lw;
-#pragma unroll
-  for (int h = 0; h < 2; h++)
-    if (hw[h].active && hw[h].e1 > hw[h].e0) {
-      const int it = hw[h].start + (int)(hw[h].e0 - hw[h].t0);
-      stop = it < stop ? it : stop;
-    }
-  // blocks of TB stages, the next block's survivor words loaded ahead
-  constexpr int TB = 8;
-  uint32_t acc[2] = {0u, 0u};
-  uint32_t wc[TB][C::WORDS], wn[TB][C::WORDS];
-  int hi = Lw;  // exclusive upper iteration of the current block
-  int lo = hi - TB > stop ? hi - TB : stop;
-  lo = lo < 0 ? 0 : lo;
-#pragma unroll
-  for (int q = 0; q < TB; q++)
-    if (lo + q < hi) load_words<C>(sl, lo + q, wc[q]);
-  while (hi > stop) {
-    const int nhi = lo, nlo = (nhi - TB > stop) ? nhi - TB : stop;
-    if (nhi > stop) {
-#pragma unroll
-      for (int q = 0; q < TB; q++)
-        if (nlo + q < nhi) load_words<C>(sl, nlo + q, wn[q]);
-    }
-#pragma unroll
-    for (int q = TB - 1; q >= 0; q--)
-      if (lo + q < hi) tb_stage<C>(lo + q, wc[q], s, acc, hw);
-#pragma unroll
-    for (int q = 0; q < TB; q++)
-#pragma unroll
-      for (int k = 0; k < C::WORDS; k++) wc[q][k] = wn[q][k];
-    hi = nhi;
-    lo = nlo;
-  }
+  traceback_pair<C>(hw, Lw, s, sl);
 }
 
 

@@ -55,7 +55,9 @@ def test_lane_routine_matches_oracle(emu, fn, code):
     K, beta, polys = code
     for i, (n, f, v, mode, ebn0) in enumerate([(5000, 1024, 48, 0, 1.0), (4102, 0, 0, 1, 3.0), (3000, 256, 20, 2, 0.0),
                                                 (7777, 512, 33, 1, 2.0), (100, 8, 40, 0, 0.5),
-                                                (64 * 200 + 13, 96, 16, 0, 6.0), (2500, 64, 3, 0, 2.0)]):
+                                                (64 * 200 + 13, 96, 16, 0, 6.0), (2500, 64, 3, 0, 2.0),
+                                                (32 * 200 + 5, 32, 10, 1, 1.0), (9000, 0, 0, 0, 3.0),
+                                                (3000, 40, 2, 1, 0.0), (1000, 512, 512, 2, 1.0)]):
         tail = K - 1 if mode == 1 else 0
         s = synth.make_stream(lambda x: oracle.encode(K, beta, polys, x), beta, n, ebn0, seed=i, tail=tail)
         want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v, mode)[: n - tail]
