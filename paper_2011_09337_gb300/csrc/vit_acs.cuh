@@ -1045,36 +1045,42 @@ __device__ void decode_pair_rot(const Half (&hw)[2], int Lw, int masked_until, u
   const int64_t te0 = sel1 ? hw[1].e0 : hw[0].e0;
   const int64_t te1 = sel1 ? hw[1].e1 : hw[0].e1;
   const int tstart = sel1 ? hw[1].start : hw[0].start;
-  uint8_t* tout = sel1 ? hw[1].out : hw[0].out;
-  const bool tracer = lig < 2 && (sel1 ? hw[1].active : hw[0].active);
+  uint8_t* const tout = (sel1 ? hw[1].out : hw[0].out) + (te0 >> 3);
+  const bool tracer = lig < 2 && (sel1 ? hw[1].active : hw[0].active) && te1 > te0;
   int st = sel1 ? s[1] : s[0];
-  int stop = Lw;
-  if (tracer && te1 > te0) stop = tstart + (int)(te0 - tt0);
+  // The tracer's emitted iterations [r0, r1).  As in the one-lane
+  // traceback, the decision read at iteration i (the bit written at slot
+  // position i mod (K-1)) is the decoded bit of iteration i - (K-1), so the
+  // accumulator a = 2a + d holds decoded bits from its low end, starting with
+  // the start state's bits in iteration order (rotated by Lw mod (K-1)).
+  const int r0 = tstart + (int)(te0 - tt0), r1 = tstart + (int)(te1 - tt0);
+  int nb = tracer ? (r1 - r0 + 7) / 8 - 1 : -1;
+  uint32_t acc = rotr_w((uint32_t)st, Lw % C::KM1, C::KM1);
+  int rmin = tracer ? r0 : Lw;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int so = __shfl_xor_sync(0xffffffffu, stop, o);
-    stop = so < stop ? so : stop;
+    const int ro = __shfl_xor_sync(0xffffffffu, rmin, o);
+    rmin = ro < rmin ? ro : rmin;
   }
-  uint32_t acc = 0;
+  tb_emit(acc, Lw - C::KM1, r0, r1, nb, tout);
+  const int ib = rmin + C::KM1;  // lowest iteration read (warp-wide)
+  if (ib >= Lw) return;
   constexpr int TB = 8;
   uint32_t wc[TB][C::WORDS], wn[TB][C::WORDS];
-  int hi = Lw;
-  int lo = hi - TB > stop ? hi - TB : stop;
-  lo = lo < 0 ? 0 : lo;
+  // blocks [lo, lo + TB) aligned to ib, the highest one cut at Lw
+  int lo = ib + TB * ((Lw - 1 - ib) / TB);
 #pragma unroll
   for (int q = 0; q < TB; q++)
-    if (lo + q < hi) load_words<C>(sl, lo + q, wc[q]);
-  while (hi > stop) {
-    const int nhi = lo, nlo = (nhi - TB > stop) ? nhi - TB : stop;
-    if (nhi > stop) {
+    if (lo + q < Lw) load_words<C>(sl, lo + q, wc[q]);
+  while (true) {
+    if (lo > ib) {
 #pragma unroll
-      for (int q = 0; q < TB; q++)
-        if (nlo + q < nhi) load_words<C>(sl, nlo + q, wn[q]);
+      for (int q = 0; q < TB; q++) load_words<C>(sl, lo - TB + q, wn[q]);
     }
 #pragma unroll
     for (int q = TB - 1; q >= 0; q--) {
       const int i = lo + q;
-      if (i >= hi) continue;
+      if (i >= Lw) continue;
       const int P = i % C::KM1;
       const int src = gbase + (st >> C::NSB);
       uint32_t ww[C::WORDS];
@@ -1084,23 +1090,16 @@ __device__ void decode_pair_rot(const Half (&hw)[2], int Lw, int masked_until, u
       const uint32_t word = pick_word<C>(ww, r);
       const uint32_t pol = (h == 0 ? 1u : 0u) ^ ((P >= C::NSB && ((st >> P) & 1)) ? 1u : 0u);
       const uint32_t d = ((word >> (16 * h + surv_pos<C>(r))) & 1u) ^ pol;
-      const uint32_t bit = (uint32_t)(st >> P) & 1u;
       st = (st & ~(1 << P)) | (int)(d << P);
-      const int64_t t = tt0 + (int64_t)(i - tstart);
-      if (tracer && t >= te0 && t < te1) {
-        acc |= bit << (t & 7);
-        if ((t & 7) == 0 || t == te0) {
-          tout[t >> 3] = (uint8_t)acc;
-          acc = 0;
-        }
-      }
+      acc = 2u * acc + d;
     }
+    tb_emit(acc, lo - C::KM1, r0, r1, nb, tout);
+    if (lo <= ib) break;
+    lo -= TB;
 #pragma unroll
     for (int q = 0; q < TB; q++)
 #pragma unroll
       for (int k = 0; k < C::WORDS; k++) wc[q][k] = wn[q][k];
-    hi = nhi;
-    lo = nlo;
   }
 }
 #endif  // __CUDACC__

@@ -649,7 +649,7 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     const vit_code* c = leaders[k];
     vit_batch::Group g;
     g.entry = c->entry;
-    g.launch = c->pt_f0 > 0 ? c->pt_launch : c->entry->launch;
+    g.launch = c->pt_f0 > 0 ? c->pt_launch : c->entry->launch;  // replaced below for short frames
     g.pt_f0 = c->pt_f0;
     g.pt_rule = c->pt_rule;
     g.pt_seed = c->pt_seed;
@@ -694,6 +694,9 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     }
     if (rc != VIT_OK) break;
     g.ntiles = tiles;
+    // frames shorter than a warp task on average: most groups of a warp are
+    // loaded with masking, and the byte-load kernel runs them faster
+    if (g.pt_f0 == 0 && tiles < (int64_t)g.nframes * c->entry->tiles_per_task) g.launch = c->entry->launch_bytes;
     const int64_t tpt = c->entry->tiles_per_task;
     g.ntasks = (tiles + tpt - 1) / tpt;
     g.task_len.assign((size_t)g.ntasks, 0);

@@ -112,13 +112,16 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane)
     decode_pair_rot<C>(hw, Lw, mu, a.M, sl, lane, words_ok);
 }
 
-// One warp per task, tasks in launch order.
-template <class C>
+// One warp per task, tasks in launch order.  kWords = false compiles the
+// byte-load path only (used for batches of short frames, where most groups
+// of a warp are loaded with masking anyway and the kernel with both paths
+// needs more registers).
+template <class C, bool kWords = true>
 __global__ void __maxnreg__(kMaxRegs) decode_tiles_kernel(const KArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t task = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (task >= a.ntasks) return;  // warp-uniform
-  run_task<C>(a, task, lane);
+  run_task<C, kWords>(a, task, lane);
 }
 
 // Persistent kernel over the tasks of two codes: each warp takes the next
@@ -166,6 +169,7 @@ struct CodeEntry {
   int unroll; // stages per unrolled group
   int tiles_per_task;
   cudaError_t (*launch)(const KArgs&, int warps, cudaStream_t);
+  cudaError_t (*launch_bytes)(const KArgs&, int warps, cudaStream_t);  // byte loads only
 };
 typedef cudaError_t (*LaunchFn)(const KArgs&, int warps, cudaStream_t);
 
@@ -196,7 +200,12 @@ cudaError_t launch_tasks(const KArgs& a, int warps, cudaStream_t s) {
 
 template <class C>
 cudaError_t launch_decode(const KArgs& a, int warps, cudaStream_t s) {
-  return launch_tasks<decode_tiles_kernel<C>>(a, warps, s);
+  return launch_tasks<decode_tiles_kernel<C, true>>(a, warps, s);
+}
+
+template <class C>
+cudaError_t launch_decode_bytes(const KArgs& a, int warps, cudaStream_t s) {
+  return launch_tasks<decode_tiles_kernel<C, false>>(a, warps, s);
 }
 
 template <class C0, class C1>
@@ -219,7 +228,8 @@ cudaError_t launch_mixed(const MixArgs& a, int warps, cudaStream_t s) {
 template <class C>
 constexpr CodeEntry make_entry() {
   return CodeEntry{C::K, C::BETA, {C::poly(0), C::poly(1), C::poly(2), C::poly(3)}, C::WORDS, C::U,
-                   64 / C::G, &launch_decode<C>};
+                   64 / C::G, &launch_decode<C>,
+                   (C::G > 1 && kWordLoads<C>) ? &launch_decode_bytes<C> : &launch_decode<C>};
 }
 #endif
 
