@@ -451,6 +451,26 @@ def large_streams_leg(vit, torch, device, steps):
     return out
 
 
+def profile_k9(vit, torch, device):
+    """Target of the K=9 ncu captures: one 2^25-bit stream decoded twice."""
+    from paper_2011_09337_gb300 import synth
+    K9, B9, P9 = synth.CODE_K9_R12
+    n = 1 << 25
+    code = vit.Code(K9, B9, P9, f=2048, v=96)
+
+    def enc(bits):
+        return vit.encode(code, torch.from_numpy(bits).to(device)).cpu().numpy()
+
+    st = synth.make_stream(enc, B9, n, 4.0, seed=9)
+    llr = torch.from_numpy(st.llr.reshape(-1)).to(device)
+    ws = torch.empty(code.workspace_bytes(n), dtype=torch.uint8, device=device)
+    o = torch.empty((n + 7) // 8, dtype=torch.uint8, device=device)
+    for _ in range(2):
+        vit.decode(code, llr, n, out=o, workspace=ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": "ok", "code": "k9", "bits": n}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,6 +485,9 @@ def main():
                     help="build the workload with --streams streams, run the planned batch twice and exit "
                          "(the target of the ncu captures)")
     ap.add_argument("--streams", type=int, default=len(EBN0))
+    ap.add_argument("--profile-code", default="k7", choices=["k7", "k9"],
+                    help="with --profile: k7 = the batch above; k9 = one 2^25-bit K=9 (561,753) stream, "
+                         "f=2048, v=96, decoded twice")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -483,6 +506,9 @@ def main():
     dev = torch.device("cuda", local)
 
     from paper_2011_09337_gb300 import vit
+    if args.profile and args.profile_code == "k9":
+        profile_k9(vit, torch, dev)
+        return
     code = vit.Code(K, BETA, POLYS, f=F, v=V)
     streams = make_inputs(vit, code, dev, torch, args.streams)
     nbytes = (NBITS + 7) // 8
