@@ -309,6 +309,38 @@ def make_mixed_batch(vit, torch, device, nframes=MIX_FRAMES, seed=2):
     return codes, frames
 
 
+def frame_latency_leg(vit, torch, device, steps):
+    """One 4096-bit frame with its 6-bit zero tail, K=7 (171,133), full-frame
+    decoding (f = 0), 3 dB: the latency of one vit_decode_ws call (one launch
+    of the tile decoder on one tile), device-resident."""
+    from paper_2011_09337_gb300 import synth
+    n = 4096 + K - 1
+    code = vit.Code(K, BETA, POLYS, f=0, v=0, mode=vit.TERMINATED)
+
+    def enc(bits):
+        return vit.encode(code, torch.from_numpy(bits).to(device)).cpu().numpy()
+
+    st = synth.make_stream(enc, BETA, n, 3.0, seed=0, tail=K - 1)
+    llr = torch.from_numpy(st.llr.reshape(-1)).to(device)
+    ws = torch.empty(code.workspace_bytes(n), dtype=torch.uint8, device=device)
+    o = torch.empty((n - K + 1 + 7) // 8, dtype=torch.uint8, device=device)
+    for _ in range(3):
+        vit.decode(code, llr, n, out=o, workspace=ws)
+    torch.cuda.synchronize()
+    reps = max(steps, 20)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        vit.decode(code, llr, n, out=o, workspace=ws)
+    b.record()
+    torch.cuda.synchronize()
+    us = a.elapsed_time(b) / reps * 1e3
+    got = synth.unpack_bits(o.cpu().numpy(), n - K + 1)
+    return {"workload": "4096 info + 6 tail bits, K=7 (171,133), terminated, f=0 (one tile), 3 dB",
+            "us_per_frame": us, "value": 4096 / us, "unit": "Mbit/s",
+            "bit_errors": int(np.sum(got != st.bits[: n - K + 1]))}
+
+
 def parallel_traceback_leg(vit, torch, frames_llr, out, steps):
     """The main workload decoded with the parallel traceback (Sec. "Parallel
     Traceback Algorithm"): subframes of 32 stages, each traced back over
@@ -595,6 +627,7 @@ def main():
     e2e_value = bits_per_step * world / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
 
     pt = None if args.no_pt else parallel_traceback_leg(vit, torch, d_llr, d_out, args.steps)
+    frame = frame_latency_leg(vit, torch, dev, args.steps)
     mixed = None if args.no_mixed else mixed_batch_leg(vit, torch, dev, args.steps)
     large = None if args.no_large else large_streams_leg(vit, torch, dev, max(3, args.steps // 4))
 
@@ -628,6 +661,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": args.steps,
         "parallel_traceback": pt,
+        "frame_latency": frame,
         "batch_mixed": mixed,
         "large_streams": large,
         "ber_6db": ber6,
