@@ -517,9 +517,9 @@ def main():
                     help="build the workload with --streams streams, run the planned batch twice and exit "
                          "(the target of the ncu captures)")
     ap.add_argument("--streams", type=int, default=len(EBN0))
-    ap.add_argument("--profile-code", default="k7", choices=["k7", "k9"],
+    ap.add_argument("--profile-code", default="k7", choices=["k7", "k9", "frame"],
                     help="with --profile: k7 = the batch above; k9 = one 2^25-bit K=9 (561,753) stream, "
-                         "f=2048, v=96, decoded twice")
+                         "f=2048, v=96, decoded twice; frame = the single-frame latency case, decoded twice")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -540,6 +540,9 @@ def main():
     from paper_2011_09337_gb300 import vit
     if args.profile and args.profile_code == "k9":
         profile_k9(vit, torch, dev)
+        return
+    if args.profile and args.profile_code == "frame":
+        print(json.dumps({"profile_run": "ok", "code": "frame", **frame_latency_leg(vit, torch, dev, 2)}))
         return
     code = vit.Code(K, BETA, POLYS, f=F, v=V)
     streams = make_inputs(vit, code, dev, torch, args.streams)

@@ -171,6 +171,23 @@ void register_pt(const MixKey& k, LaunchFn launch) {
   pt_registry().push_back(PtReg{k, launch});
 }
 
+std::vector<PtReg>& warp_registry() {
+  static std::vector<PtReg> r;
+  return r;
+}
+
+void register_warp(const MixKey& k, LaunchFn launch) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  warp_registry().push_back(PtReg{k, launch});
+}
+
+LaunchFn find_warp(const CodeEntry* e) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (const PtReg& r : warp_registry())
+    if (key_matches(r.key, e)) return r.launch;
+  return nullptr;
+}
+
 LaunchFn find_pt(const CodeEntry* e) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   for (const PtReg& r : pt_registry())
@@ -238,6 +255,7 @@ int vit_create(vit_code** out, int K, int beta, const uint32_t* polys, int64_t f
   c->v1 = c->v2 = v;
   c->mode = VIT_STREAM;
   c->entry = e;
+  c->warp_launch = find_warp(e);
   *out = c;
   return VIT_OK;
 }
@@ -389,7 +407,11 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
     a.pt_nsub = pt_subframes(c, n);
     a.pt_states = p;
   }
-  cudaError_t e = (c->pt_f0 > 0 ? c->pt_launch : c->entry->launch)(a, kWarpsPerCta, s);
+  LaunchFn launch = c->pt_f0 > 0 ? c->pt_launch : c->entry->launch;
+  // few short tiles: one warp per tile decodes them with lower latency
+  if (c->pt_f0 == 0 && c->warp_launch != nullptr && tiles <= kWarpTileLimit && max_window(c, n) <= kWarpSmemStages)
+    launch = c->warp_launch;
+  cudaError_t e = launch(a, kWarpsPerCta, s);
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   return VIT_OK;
 }

@@ -14,6 +14,11 @@ constexpr int kMaxRegs = 168;     // registers per thread of the tile decoders
 // CTAs of 4 warps share an SM, so a 2^26-bit K=9 stream (2048 warp tasks)
 // runs in one wave (2.90 ms against 3.31 ms at 168 registers and 3 CTAs).
 constexpr int kMaxRegsRotWords = 128;
+// Single frames of at most kWarpTileLimit tiles whose windows fit
+// kWarpSmemStages stages (48 KB of 64-bit decision words per warp) are
+// decoded one warp per tile (lower latency than 64 tiles per warp).
+constexpr int kWarpSmemStages = 6144;
+constexpr int64_t kWarpTileLimit = 1024;
 
 // Arguments of the tile decoder.  A "task" is one warp: 32 lanes x 2 tiles.
 struct KArgs {
@@ -258,6 +263,9 @@ const MixEntry* find_mixed(const CodeEntry* a, const CodeEntry* b, bool* swapped
 // Tile decoders with the parallel traceback, registered by (K, beta, polys).
 void register_pt(const MixKey& k, LaunchFn launch);
 LaunchFn find_pt(const CodeEntry* e);
+// Warp-per-tile decoders for frames with few tiles, by (K, beta, polys).
+void register_warp(const MixKey& k, LaunchFn launch);
+LaunchFn find_warp(const CodeEntry* e);
 
 }  // namespace vit
 
@@ -274,6 +282,7 @@ struct vit_code {
   int pt_rule;        // VIT_PT_STORED or VIT_PT_RANDOM
   uint64_t pt_seed;
   vit::LaunchFn pt_launch;
+  vit::LaunchFn warp_launch;  // warp-per-tile decoder, or nullptr
 };
 
 namespace vit {
