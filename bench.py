@@ -206,7 +206,8 @@ def algorithmic_ops_per_step() -> float:
 
 def cpu_oracle_rate(seconds: float = 12.0):
     """Times the oracle's tiled decoder on a bounded sample of the workload with
-    all host cores (ctypes releases the GIL).  Returns (Mbit/s, cores, sample)."""
+    all host cores (ctypes releases the GIL).  Returns (Mbit/s, cores, sample,
+    single-core Mbit/s from the 4-tile calibration run on one thread)."""
     import oracle
     from paper_2011_09337_gb300 import synth
 
@@ -227,7 +228,8 @@ def cpu_oracle_rate(seconds: float = 12.0):
     for t in threads:
         t.join()
     dt = time.perf_counter() - t0
-    return ntiles * F / dt / 1e6, cores, f"{ntiles} tiles of 1024 bits (f=1024, v=48, 3 dB) on {cores} threads"
+    return (ntiles * F / dt / 1e6, cores, f"{ntiles} tiles of 1024 bits (f=1024, v=48, 3 dB) on {cores} threads",
+            F / per_tile / 1e6)
 
 
 def run_reference(args):
@@ -672,8 +674,9 @@ def main():
     if clocks.get("sm_mhz"):
         line["roofline"]["frac_at_sampled_clock"] = achieved_tops / (peak_tops * clocks["sm_mhz"] / sm_max)
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
-        v, cores, sample = cpu_oracle_rate()
-        line["cpu_baseline"] = {"value": v, "unit": "Mbit/s", "cores": cores, "kind": "oracle", "sample": sample}
+        v, cores, sample, v1 = cpu_oracle_rate()
+        line["cpu_baseline"] = {"value": v, "unit": "Mbit/s", "cores": cores, "kind": "oracle", "sample": sample,
+                                "single_core": {"value": v1, "unit": "Mbit/s", "sample": "4 tiles on 1 thread"}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
