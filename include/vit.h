@@ -171,10 +171,10 @@ int vit_hard_llr(const uint8_t* bits, int64_t count, int8_t* llr, vit_stream_t s
 
 typedef struct {
   const vit_code* code; /* any created code; frames may mix codes */
-  const int8_t* llr;    /* device, vit_llr_count(code, n) int8 values */
+  const int8_t* llr;    /* device (page-locked host with VIT_BATCH_HOST), vit_llr_count(code, n) int8 values */
   int64_t n;            /* trellis stages, >= 1 */
   int mode;             /* VIT_STREAM, VIT_TERMINATED or VIT_FREE_START */
-  uint8_t* bits_out;    /* device, ceil(vit_output_bits / 8) bytes */
+  uint8_t* bits_out;    /* device (page-locked host with VIT_BATCH_HOST), ceil(vit_output_bits / 8) bytes */
 } vit_frame;
 
 /*
@@ -192,9 +192,27 @@ typedef struct {
  * exactly two code groups for which a persistent two-code kernel is
  * compiled, one launch pulls all their warp tasks from a queue ordered
  * longest window first (otherwise ignored).  Bits 8..15 give the CTA size in
- * warps (1..8, 0 = 4).  Other bits: VIT_EINVAL.
+ * warps (1..8, 0 = 4).
+ *
+ * VIT_BATCH_HOST (host-staged batch): every frame's llr and bits_out are
+ * HOST pointers to page-locked memory (cudaHostAlloc / cudaHostRegister;
+ * anything else gives VIT_EINVAL at plan time).  The plan owns device copies
+ * of the frames' LLRs and output bytes, and each run copies the LLRs in,
+ * decodes and copies the bits back, pipelined: every group's warp tasks are
+ * cut into chunks (bits 16..23: 1..64 chunks, 0 = 8; a chunk count without
+ * VIT_BATCH_HOST is VIT_EINVAL); chunk k's input copy (a plan-owned copy
+ * stream), its decode launch (one of up to four plan-owned compute streams,
+ * in turn) and its output copy (a second copy stream) are ordered by events,
+ * so the copies of some chunks overlap the decoding of others.  Each chunk
+ * copies the LLR bytes of its tiles' windows that earlier chunks have not
+ * copied, and the output bytes its tiles emit (tiles end on byte boundaries,
+ * so no byte is shared between chunks).  Punctured frames are copied whole
+ * and de-punctured before the first chunk.  All of it is forked from and
+ * joined back into the caller's stream: when that stream reaches the end of
+ * the run, the host output buffers hold the bits.  VIT_BATCH_PERSISTENT is
+ * ignored with VIT_BATCH_HOST.  Other bits: VIT_EINVAL.
  */
-enum { VIT_BATCH_GRAPH = 1, VIT_BATCH_PERSISTENT = 4 };
+enum { VIT_BATCH_GRAPH = 1, VIT_BATCH_PERSISTENT = 4, VIT_BATCH_HOST = 8 };
 int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int flags);
 int vit_batch_run(vit_batch* batch, vit_stream_t stream);
 void vit_batch_destroy(vit_batch* batch);

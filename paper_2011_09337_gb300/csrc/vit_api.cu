@@ -505,6 +505,17 @@ struct vit_batch {
     int64_t* d_tile0 = nullptr;
     uint32_t* d_slab = nullptr;
     std::vector<int64_t> task_len;  // host estimate of each task's window length
+    std::vector<Frame> hframes;     // host copy of the frame table
+    std::vector<int64_t> htile0;
+    struct IO {                     // VIT_BATCH_HOST: host buffers and their device copies
+      const int8_t* h_llr;
+      uint8_t* h_out;
+      int8_t* d_llr;
+      uint8_t* d_out;
+      int64_t llr_bytes, out_bytes;
+      bool punctured;
+    };
+    std::vector<IO> io;
   };
   struct Dep {
     const int8_t* src;
@@ -512,8 +523,27 @@ struct vit_batch {
     int64_t n;
     PunctArgs pa;
   };
+  // host-staged runs (VIT_BATCH_HOST): one contiguous copy of host memory
+  struct Copy {
+    const void* src;
+    void* dst;
+    size_t bytes;
+  };
+  // a chunk: warp tasks [lo, hi) of one group, the LLR bytes they need that
+  // earlier chunks have not copied, and the output bytes they complete
+  struct Chunk {
+    int group;
+    int64_t lo, hi;
+    std::vector<Copy> in, out;
+  };
   std::vector<Group> groups;
   std::vector<Dep> deps;
+  std::vector<Copy> host_in;  // whole punctured frames, copied before the chunks
+  std::vector<Chunk> chunks;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  std::vector<cudaStream_t> comp;        // compute streams, chunks in turn
+  std::vector<cudaEvent_t> ev_in, ev_dec;  // per chunk
+  cudaEvent_t ev_end = nullptr;
   // one stream and completion event per group after the first: the groups
   // run concurrently (fork/join with events, also inside a captured graph)
   std::vector<cudaStream_t> side;
@@ -554,6 +584,12 @@ void batch_free(vit_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaStream_t x : b->side) cudaStreamDestroy(x);
   for (cudaEvent_t x : b->done) cudaEventDestroy(x);
+  for (cudaStream_t x : b->comp) cudaStreamDestroy(x);
+  for (cudaEvent_t x : b->ev_in) cudaEventDestroy(x);
+  for (cudaEvent_t x : b->ev_dec) cudaEventDestroy(x);
+  if (b->copy_in) cudaStreamDestroy(b->copy_in);
+  if (b->copy_out) cudaStreamDestroy(b->copy_out);
+  if (b->ev_end) cudaEventDestroy(b->ev_end);
   if (b->fork) cudaEventDestroy(b->fork);
   for (void* p : b->allocs) cudaFree(p);
   delete b;
@@ -579,7 +615,57 @@ KArgs group_args(const vit_batch::Group& g) {
   return a;
 }
 
+// Host-staged run: input copies on copy_in, chunk launches on the compute
+// streams in turn, output copies on copy_out, ordered per chunk by events;
+// forked from and joined back into the caller's stream.
+int batch_enqueue_host(vit_batch* b, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->copy_in, b->fork, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->copy_out, b->fork, 0);
+  for (size_t j = 0; j < b->comp.size() && e == cudaSuccess; j++) e = cudaStreamWaitEvent(b->comp[j], b->fork, 0);
+  for (const auto& c : b->host_in)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, b->copy_in);
+  if (e != cudaSuccess) return cuda_fail(e, "host batch input");
+  for (const auto& d : b->deps) {
+    const unsigned grid = (unsigned)((d.n + 255) / 256);
+    depuncture_kernel<<<grid, 256, 0, b->copy_in>>>(d.src, d.n, d.dst, d.pa);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "depuncture launch");
+  }
+  for (size_t k = 0; k < b->chunks.size() && e == cudaSuccess; k++) {
+    const auto& ch = b->chunks[k];
+    for (const auto& c : ch.in)
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, b->copy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_in[k], b->copy_in);
+    cudaStream_t cs = b->comp[k % b->comp.size()];
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b->ev_in[k], 0);
+    if (e == cudaSuccess) {
+      KArgs a = group_args(b->groups[(size_t)ch.group]);
+      a.task_base = ch.lo;
+      a.ntasks = ch.hi;
+      e = b->groups[(size_t)ch.group].launch(a, b->warps, cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_dec[k], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->copy_out, b->ev_dec[k], 0);
+    for (const auto& c : ch.out)
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, b->copy_out);
+  }
+  // join every plan stream back into the caller's stream (copy_out's end
+  // already follows all of them; the direct joins keep graph capture happy)
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_end, b->copy_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_end, 0);
+  const size_t nk = b->chunks.size();
+  if (e == cudaSuccess && nk > 0) e = cudaStreamWaitEvent(s, b->ev_in[nk - 1], 0);
+  for (size_t j = 0; j < b->comp.size() && j < nk && e == cudaSuccess; j++) {
+    const size_t last = j + (nk - 1 - j) / b->comp.size() * b->comp.size();  // last chunk on comp[j]
+    e = cudaStreamWaitEvent(s, b->ev_dec[last], 0);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "host batch");
+  return VIT_OK;
+}
+
 int batch_enqueue(vit_batch* b, cudaStream_t s) {
+  if (b->flags & VIT_BATCH_HOST) return batch_enqueue_host(b, s);
   for (const auto& d : b->deps) {
     const unsigned grid = (unsigned)((d.n + 255) / 256);
     depuncture_kernel<<<grid, 256, 0, s>>>(d.src, d.n, d.dst, d.pa);
@@ -614,6 +700,70 @@ int batch_enqueue(vit_batch* b, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");
   return VIT_OK;
 }
+// Cuts every group's warp tasks into up to `nchunks` chunks (round-robin over
+// the groups) and lists each chunk's copies; creates the plan's streams and
+// events for host-staged runs.
+int plan_host_chunks(vit_batch* b, int nchunks) {
+  for (auto& g : b->groups)
+    for (const auto& io : g.io)
+      if (io.punctured) b->host_in.push_back(vit_batch::Copy{io.h_llr, io.d_llr, (size_t)io.llr_bytes});
+  std::vector<std::vector<int64_t>> mark(b->groups.size());  // LLR bytes copied so far, per frame
+  for (size_t gi = 0; gi < b->groups.size(); gi++) mark[gi].assign(b->groups[gi].io.size(), 0);
+  for (int c = 0; c < nchunks; c++) {
+    for (size_t gi = 0; gi < b->groups.size(); gi++) {
+      const auto& g = b->groups[gi];
+      const int64_t ng = g.ntasks < nchunks ? g.ntasks : nchunks;
+      if (c >= ng) continue;
+      vit_batch::Chunk ch;
+      ch.group = (int)gi;
+      ch.lo = g.ntasks * c / ng;
+      ch.hi = g.ntasks * (c + 1) / ng;
+      const int64_t tpt = g.entry->tiles_per_task;
+      const int64_t t_lo = ch.lo * tpt, t_hi = ch.hi * tpt < g.ntiles ? ch.hi * tpt : g.ntiles;
+      for (size_t j = 0; j < g.hframes.size(); j++) {
+        const Frame& fr = g.hframes[j];
+        const auto& io = g.io[j];
+        const int64_t ft0 = g.htile0[j], nt = tile_count(fr.n, g.tl.f);
+        const int64_t a = (t_lo > ft0 ? t_lo : ft0) - ft0, z = (t_hi < ft0 + nt ? t_hi : ft0 + nt) - ft0;
+        if (a >= z) continue;
+        const Half ha = make_half(fr, a, g.tl), hz = make_half(fr, z - 1, g.tl);
+        if (!io.punctured) {
+          const int beta = g.entry->beta;
+          int64_t lo = ha.t0 * beta;
+          const int64_t hi = hz.t1 * beta;
+          lo = lo > mark[gi][j] ? lo : mark[gi][j];
+          if (hi > lo) ch.in.push_back(vit_batch::Copy{io.h_llr + lo, io.d_llr + lo, (size_t)(hi - lo)});
+          if (hi > mark[gi][j]) mark[gi][j] = hi;
+        }
+        if (hz.e1 > ha.e0) {
+          const int64_t o0 = ha.e0 / 8, o1 = (hz.e1 + 7) / 8;
+          ch.out.push_back(vit_batch::Copy{io.d_out + o0, io.h_out + o0, (size_t)(o1 - o0)});
+        }
+      }
+      b->chunks.push_back(std::move(ch));
+    }
+  }
+  const size_t nk = b->chunks.size();
+  const size_t ncomp = nk < 4 ? nk : 4;
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_end, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->copy_out, cudaStreamNonBlocking);
+  for (size_t j = 0; j < ncomp && e == cudaSuccess; j++) {
+    cudaStream_t x = nullptr;
+    e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->comp.push_back(x);
+  }
+  for (size_t k = 0; k < nk && e == cudaSuccess; k++) {
+    cudaEvent_t x = nullptr, y = nullptr;
+    e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ev_in.push_back(x);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&y, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ev_dec.push_back(y);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "host batch streams");
+  return VIT_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -631,9 +781,30 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     if (f.mode == VIT_TERMINATED && f.n <= f.code->K - 1)
       return fail(VIT_EINVAL, "frame %d: terminated frame shorter than its tail", i);
   }
-  if (flags & ~(VIT_BATCH_GRAPH | VIT_BATCH_PERSISTENT | 0xff00)) return fail(VIT_EINVAL, "unknown batch flag");
+  if (flags & ~(VIT_BATCH_GRAPH | VIT_BATCH_PERSISTENT | VIT_BATCH_HOST | 0xff00 | 0xff0000))
+    return fail(VIT_EINVAL, "unknown batch flag");
   const int warps = (flags >> 8) & 0xff;
   if (warps != 0 && (warps < 1 || warps > 8)) return fail(VIT_EINVAL, "warps per CTA must be in [1, 8]");
+  const bool host = (flags & VIT_BATCH_HOST) != 0;
+  int nchunks = (flags >> 16) & 0xff;
+  if (nchunks != 0 && !host) return fail(VIT_EINVAL, "a chunk count needs VIT_BATCH_HOST");
+  if (nchunks > 64) return fail(VIT_EINVAL, "chunks must be in [1, 64]");
+  if (nchunks == 0) nchunks = 8;
+  if (host) {
+    // page-locked host memory only: pageable buffers would make the copies
+    // synchronous, and device buffers belong to the ordinary batch
+    auto pinned = [](const void* p) {
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      return at.type == cudaMemoryTypeHost;
+    };
+    for (int i = 0; i < nframes; i++)
+      if (!pinned(frames[i].llr) || !pinned(frames[i].bits_out))
+        return fail(VIT_EINVAL, "frame %d: VIT_BATCH_HOST wants page-locked host buffers", i);
+  }
   vit_batch* b = new (std::nothrow) vit_batch;
   if (b == nullptr) return fail(VIT_ENOMEM, "out of host memory");
   b->flags = flags;
@@ -686,19 +857,34 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
       const vit_frame& f = frames[members[k][j]];
       const vit_code* fc = f.code;
       const int8_t* llr = f.llr;
+      uint8_t* out = f.bits_out;
+      const int64_t n_out = (f.mode == VIT_TERMINATED) ? f.n - (fc->K - 1) : f.n;
+      if (host) {
+        vit_batch::Group::IO io{f.llr, f.bits_out, nullptr, nullptr, kept_in(fc, f.n), (n_out + 7) / 8,
+                                fc->period != 0};
+        io.d_llr = (int8_t*)dalloc((size_t)io.llr_bytes);
+        io.d_out = (uint8_t*)dalloc((size_t)io.out_bytes);
+        if (io.d_llr == nullptr || io.d_out == nullptr) {
+          rc = fail(VIT_ENOMEM, "device allocation failed");
+          break;
+        }
+        llr = io.d_llr;
+        out = io.d_out;
+        g.io.push_back(io);
+      }
       if (fc->period) {
         int8_t* dst = (int8_t*)dalloc((size_t)f.n * fc->beta);
         if (dst == nullptr) {
           rc = fail(VIT_ENOMEM, "device allocation failed");
           break;
         }
-        b->deps.push_back(vit_batch::Dep{f.llr, dst, f.n, make_punct(fc)});
+        b->deps.push_back(vit_batch::Dep{llr, dst, f.n, make_punct(fc)});
         llr = dst;
       }
       hf[j].llr = llr;
-      hf[j].out = f.bits_out;
+      hf[j].out = out;
       hf[j].n = f.n;
-      hf[j].n_out = (f.mode == VIT_TERMINATED) ? f.n - (fc->K - 1) : f.n;
+      hf[j].n_out = n_out;
       hf[j].mode = f.mode;
       ht0[j] = tiles;
       const int64_t nt = tile_count(f.n, c->f);
@@ -742,6 +928,8 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
       rc = cuda_fail(e, "plan upload");
       break;
     }
+    g.hframes = hf;
+    g.htile0 = ht0;
     b->groups.push_back(std::move(g));
   }
   // costliest group first (it is launched on the caller's stream, first)
@@ -756,7 +944,8 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
   }
   // with VIT_BATCH_PERSISTENT, two code groups with a compiled persistent
   // kernel become one launch over a queue of all their tasks, longest first
-  if (rc == VIT_OK && (flags & VIT_BATCH_PERSISTENT) && b->groups.size() == 2 && b->groups[0].pt_f0 == 0 &&
+  if (rc == VIT_OK && host) rc = plan_host_chunks(b, nchunks);
+  if (rc == VIT_OK && !host && (flags & VIT_BATCH_PERSISTENT) && b->groups.size() == 2 && b->groups[0].pt_f0 == 0 &&
       b->groups[1].pt_f0 == 0) {
     bool swapped = false;
     const MixEntry* mx = find_mixed(b->groups[0].entry, b->groups[1].entry, &swapped);
@@ -789,7 +978,7 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
       }
     }
   }
-  if (rc == VIT_OK && b->mix == nullptr && b->groups.size() > 1) {
+  if (rc == VIT_OK && !host && b->mix == nullptr && b->groups.size() > 1) {
     cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; k++) {
       cudaStream_t x = nullptr;

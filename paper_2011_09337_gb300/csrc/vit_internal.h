@@ -189,13 +189,14 @@ struct MixEntry {
 };
 
 #if defined(__CUDACC__)
-// Launches `kernel` over the tasks of `a`, one warp per task (grid.x is
-// limited to 2^31-1 CTAs, so very large launches are split).
+// Launches `kernel` over the tasks [a.task_base, a.ntasks) of `a`, one warp
+// per task (grid.x is limited to 2^31-1 CTAs, so very large launches are
+// split).
 template <void (*kernel)(const KArgs)>
 cudaError_t launch_tasks(const KArgs& a, int warps, cudaStream_t s) {
   if (warps < 1 || warps > 8) warps = kWarpsPerCta;
   const int64_t maxc = (int64_t)1 << 30;
-  for (int64_t t0 = 0; t0 < a.ntasks; t0 += maxc * warps) {
+  for (int64_t t0 = a.task_base; t0 < a.ntasks; t0 += maxc * warps) {
     KArgs b = a;
     b.task_base = t0;
     const int64_t tasks = (a.ntasks - t0 < maxc * warps) ? a.ntasks - t0 : maxc * warps;

@@ -16,7 +16,7 @@ import torch
 from . import build_lib
 
 STREAM, TERMINATED, FREE_START = 0, 1, 2
-BATCH_GRAPH, BATCH_PERSISTENT = 1, 4
+BATCH_GRAPH, BATCH_PERSISTENT, BATCH_HOST = 1, 4, 8
 PT_STORED, PT_RANDOM = 0, 1
 
 _lib = None
@@ -208,16 +208,27 @@ class Batch:
     buffers every time ``run()`` is called; ``graph=True`` replays one
     captured CUDA graph.  Code groups run as concurrent launches, or with
     ``persistent=True`` (two groups with a compiled two-code kernel) as one
-    persistent launch over a shared task queue."""
+    persistent launch over a shared task queue.  With ``host=True``
+    (VIT_BATCH_HOST) the tensors are pinned CPU tensors: each run copies the
+    LLRs in, decodes and copies the bits back, pipelined over ``chunks``
+    chunks (0 = library default)."""
 
-    def __init__(self, frames, graph: bool = True, warps: int = 0, persistent: bool = False):
-        """frames: iterable of (code, llr, n, mode, out) with CUDA tensors;
-        warps: CTA size in warps (1..8, 0 = library default)."""
+    def __init__(self, frames, graph: bool = True, warps: int = 0, persistent: bool = False,
+                 host: bool = False, chunks: int = 0, device=None):
+        """frames: iterable of (code, llr, n, mode, out) with CUDA tensors
+        (pinned CPU tensors with host=True); warps: CTA size in warps (1..8,
+        0 = library default); device: the CUDA device of a host batch
+        (default: the current one)."""
         L = load()
         self._keep = []
         arr = (_Frame * len(frames))()
         for i, (code, llr, n, mode, out) in enumerate(frames):
-            if not (llr.is_cuda and llr.dtype == torch.int8 and llr.is_contiguous()):
+            if host:
+                if not (not llr.is_cuda and llr.is_pinned() and llr.dtype == torch.int8 and llr.is_contiguous()):
+                    raise ValueError("host batch: llr must be a contiguous pinned int8 CPU tensor")
+                if not (not out.is_cuda and out.is_pinned() and out.dtype == torch.uint8 and out.is_contiguous()):
+                    raise ValueError("host batch: out must be a contiguous pinned uint8 CPU tensor")
+            elif not (llr.is_cuda and llr.dtype == torch.int8 and llr.is_contiguous()):
                 raise ValueError("llr must be a contiguous int8 CUDA tensor")
             if llr.numel() != code.llr_count(n):
                 raise ValueError(f"frame {i}: expected {code.llr_count(n)} LLRs, got {llr.numel()}")
@@ -227,10 +238,14 @@ class Batch:
             arr[i] = _Frame(code.handle.value, llr.data_ptr(), n, mode, out.data_ptr())
             self._keep.append((code, llr, out))
         h = ctypes.c_void_p()
-        flags = (BATCH_GRAPH if graph else 0) | (BATCH_PERSISTENT if persistent else 0) | ((int(warps) & 0xFF) << 8)
+        flags = ((BATCH_GRAPH if graph else 0) | (BATCH_PERSISTENT if persistent else 0) | (BATCH_HOST if host else 0)
+                 | ((int(warps) & 0xFF) << 8) | ((int(chunks) & 0xFF) << 16))
         _check(L.vit_batch_plan(ctypes.byref(h), arr, len(frames), flags))
         self._h = h
-        self.device = frames[0][1].device
+        if host:
+            self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        else:
+            self.device = frames[0][1].device
 
     def run(self):
         _check(load().vit_batch_run(self._h, _stream(self.device)))

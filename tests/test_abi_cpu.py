@@ -126,7 +126,8 @@ def test_batch_plan_rejects_bad_arguments_before_any_device_call(lib):
     out = ctypes.c_void_p()
     fake = 0x1000  # never dereferenced: every check below fails first
     frames = (_VitFrame * 2)(_VitFrame(h.value, fake, 5000, 0, fake), _VitFrame(h.value, fake, 70, 1, fake))
-    for flags, msg in ((2, b"flag"), (1 << 16, b"flag"), (9 << 8, b"warps")):
+    for flags, msg in ((2, b"flag"), (1 << 24, b"flag"), (9 << 8, b"warps"), (1 << 16, b"VIT_BATCH_HOST"),
+                       (8 | (65 << 16), b"chunks"), (8, b"page-locked")):
         assert plan(ctypes.byref(out), ctypes.cast(frames, ctypes.c_void_p), 2, flags) == -1
         assert msg in lib.vit_last_error() and not out.value
     bad = (_VitFrame * 1)(_VitFrame(h.value, fake, 5000, 7, fake))
