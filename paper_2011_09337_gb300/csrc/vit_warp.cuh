@@ -6,8 +6,8 @@
 // l holds the path metrics of states l and l + 32 (S = 64) or of state l
 // (S <= 32) of one tile, so a stage is one butterfly per lane: the metrics of
 // the two predecessors (Eq. 3) come from their lanes by shuffle, the
-// decisions (Eq. 4) of all states by ballot, and one lane writes them as a
-// 64-bit word per stage.  Metrics are 32-bit and compared by signed
+// decisions (Eq. 4) of all states by ballot, a 64-bit word per stage.
+// Metrics are 32-bit and compared by signed
 // difference, so they may wrap; decisions and the traceback start (argmax,
 // ties to the lowest state, Alg. 2) are those of unbounded integers.  The
 // decision words of the window stay in the warp's shared memory, so windows
@@ -27,12 +27,53 @@ __device__ __forceinline__ int warp_delta(const int (&l)[C::BETA], uint32_t c) {
   return d;
 }
 
+// The beta LLR bytes of window iteration i (bytes of one 32-bit word).
+template <class C>
+__device__ __forceinline__ uint32_t warp_llr_word(const int8_t* llr, int i, int L) {
+  uint32_t w = 0;
+  if (i < L) {
+#pragma unroll
+    for (int b = 0; b < C::BETA; b++) w |= (uint32_t)(uint8_t)ld_s8(llr + (int64_t)i * C::BETA + b) << (8 * b);
+  }
+  return w;
+}
+
+// One trellis stage (Eq. 3, Eq. 4) of the warp's tile: `pk` holds the
+// stage's LLR bytes, m the lane's metrics; returns the two ballot words.
+template <class C>
+__device__ __forceinline__ void warp_stage(uint32_t (&m)[C::S > 32 ? 2 : 1], uint32_t pk, int src0, int src1,
+                                           int reg, bool live, const uint32_t (&cA)[C::S > 32 ? 2 : 1],
+                                           const uint32_t (&cB)[C::S > 32 ? 2 : 1], uint32_t (&bal)[2]) {
+  constexpr int R = C::S > 32 ? 2 : 1;
+  int l[C::BETA];
+#pragma unroll
+  for (int b = 0; b < C::BETA; b++) l[b] = (int)(int8_t)(uint8_t)(pk >> (8 * b));
+  // metrics of the two predecessors: register `reg` of lanes src0, src1
+  uint32_t q0 = __shfl_sync(0xffffffffu, m[0], src0), q1 = __shfl_sync(0xffffffffu, m[0], src1);
+  if constexpr (R == 2) {
+    const uint32_t u0 = __shfl_sync(0xffffffffu, m[1], src0), u1 = __shfl_sync(0xffffffffu, m[1], src1);
+    q0 = reg ? u0 : q0;
+    q1 = reg ? u1 : q1;
+  }
+  bal[1] = 0u;
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const uint32_t x0 = q0 + (uint32_t)warp_delta<C>(l, cA[r]), x1 = q1 + (uint32_t)warp_delta<C>(l, cB[r]);
+    const bool d = live && (int)(x1 - x0) > 0;  // ties keep the even predecessor
+    bal[r] = __ballot_sync(0xffffffffu, d);
+    m[r] = d ? x1 : x0;
+  }
+}
+
 // Decodes tile `h` (window [t0, t1), emitted [e0, e1)) with the calling warp.
 // dec: the tile's decision words, one 64-bit word per stage of the window
-// (shared memory).
+// (shared memory).  The window's LLRs arrive 32 stages at a time (lane l
+// loads stage i0 + l, one block ahead) and each stage takes its bytes by
+// shuffle, off the metrics' dependency chain; lane l keeps the decision
+// word of stage i0 + l and the warp stores a block's words together.
 template <class C>
 __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int lane) {
-  static_assert(C::S <= 64, "states of one tile over the 32 lanes");
+  static_assert(C::S <= 64 && C::BETA <= 4, "states of one tile over the 32 lanes; LLR bytes in one word");
   constexpr int S = C::S;
   constexpr int R = S > 32 ? 2 : 1;  // states per lane
   const int L = (int)(h.t1 - h.t0);
@@ -56,26 +97,31 @@ __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int l
   }
   const bool live = lane < S;
   const int8_t* llr = h.llr + h.t0 * C::BETA;
-  for (int i = 0; i < L; i++) {
-    int l[C::BETA];
+  uint32_t nxt = warp_llr_word<C>(llr, lane, L);
+  int i0 = 0;
+  for (; i0 + 32 <= L; i0 += 32) {  // whole blocks of 32 stages
+    const uint32_t cur = nxt;
+    nxt = warp_llr_word<C>(llr, i0 + 32 + lane, L);
+    uint32_t kA = 0u, kB = 0u;
 #pragma unroll
-    for (int b = 0; b < C::BETA; b++) l[b] = ld_s8(llr + (int64_t)i * C::BETA + b);
-    // metrics of the two predecessors: register `reg` of lanes src0, src1
-    uint32_t q0 = __shfl_sync(0xffffffffu, m[0], src0), q1 = __shfl_sync(0xffffffffu, m[0], src1);
-    if constexpr (R == 2) {
-      const uint32_t u0 = __shfl_sync(0xffffffffu, m[1], src0), u1 = __shfl_sync(0xffffffffu, m[1], src1);
-      q0 = reg ? u0 : q0;
-      q1 = reg ? u1 : q1;
+    for (int k = 0; k < 32; k++) {
+      uint32_t bal[2];
+      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), src0, src1, reg, live, cA, cB, bal);
+      kA = lane == k ? bal[0] : kA;
+      kB = lane == k ? bal[1] : kB;
     }
-    uint32_t bal[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-      const uint32_t x0 = q0 + (uint32_t)warp_delta<C>(l, cA[r]), x1 = q1 + (uint32_t)warp_delta<C>(l, cB[r]);
-      const bool d = live && (int)(x1 - x0) > 0;  // ties keep the even predecessor
-      bal[r] = __ballot_sync(0xffffffffu, d);
-      m[r] = d ? x1 : x0;
+    dec[i0 + lane] = (uint64_t)kA | ((uint64_t)kB << 32);
+  }
+  if (i0 < L) {  // the last, partial block
+    const uint32_t cur = nxt;
+    uint32_t kA = 0u, kB = 0u;
+    for (int k = 0; k < L - i0; k++) {
+      uint32_t bal[2];
+      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), src0, src1, reg, live, cA, cB, bal);
+      kA = lane == k ? bal[0] : kA;
+      kB = lane == k ? bal[1] : kB;
     }
-    if (lane == 0) dec[i] = (uint64_t)bal[0] | (R == 2 ? (uint64_t)bal[R - 1] << 32 : 0ull);
+    if (i0 + lane < L) dec[i0 + lane] = (uint64_t)kA | ((uint64_t)kB << 32);
   }
   // traceback start: argmax (ties to the lowest state) relative to state 0
   int best = lane;
@@ -98,32 +144,27 @@ __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int l
     }
   }
   __syncwarp();
-  if (lane != 0) return;
-  // Alg. 2 over the window, the bytes of [e0, e1) written as they complete;
-  // the next 8 decision words are loaded ahead of the dependent steps
-  uint32_t j = h.end_zero ? 0u : (uint32_t)best;
-  uint32_t acc = 0;
-  int i = L - 1;
-  const int stop = (int)(h.e0 - h.t0);
-  while (i >= stop) {
+  if (lane != 0 || h.e1 <= h.e0) return;
+  // Alg. 2 as in the tile decoder's traceback: following decision d from
+  // state j gives 2j + d, so the decision read at iteration i is the decoded
+  // bit of iteration i - (K-1); J = 2J + d kept unmasked holds the decoded
+  // bits from its low end, and the bytes of [e0, e1) are taken from J at
+  // checkpoints every 8 iterations.
+  const int r0 = (int)(h.e0 - h.t0), r1 = (int)(h.e1 - h.t0);
+  int nb = (r1 - r0 + 7) / 8 - 1;
+  uint8_t* const out = h.out + (h.e0 >> 3);
+  uint32_t J = h.end_zero ? 0u : (uint32_t)best;
+  tb_emit(J, L - C::KM1, r0, r1, nb, out);  // bytes made of start-state bits only
+  const int ib = r0 + C::KM1;               // lowest iteration read
+  for (int i = L - 1; i >= ib; i -= 8) {
     uint64_t w[8];
 #pragma unroll
-    for (int k = 0; k < 8; k++) w[k] = (i - k >= stop) ? dec[i - k] : 0ull;
+    for (int k = 0; k < 8; k++) w[k] = (i - k >= ib) ? dec[i - k] : 0ull;
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-      if (i < stop) break;
-      const int64_t t = h.t0 + i;
-      const uint32_t d = (uint32_t)(w[k] >> j) & 1u;
-      if (t < h.e1) {
-        acc |= ((j >> (C::K - 2)) & 1u) << (t & 7);
-        if ((t & 7) == 0 || t == h.e0) {
-          h.out[t >> 3] = (uint8_t)acc;
-          acc = 0u;
-        }
-      }
-      j = ((j << 1) | d) & (uint32_t)(S - 1);
-      i--;
-    }
+    for (int k = 0; k < 8; k++)
+      if (i - k >= ib) J = 2u * J + (uint32_t)((w[k] >> (J & (uint32_t)(S - 1))) & 1ull);
+    const int lo = (i - 7 > ib ? i - 7 : ib);  // lowest iteration read so far
+    tb_emit(J, lo - C::KM1, r0, r1, nb, out);
   }
 }
 #endif
