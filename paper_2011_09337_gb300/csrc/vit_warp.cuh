@@ -3,15 +3,16 @@
 //
 // The tile decoder gives each lane two whole tiles, which is the fast way to
 // decode many tiles but leaves a warp with one tile 31 idle lanes.  Here lane
-// l holds the path metrics of states l and l + 32 (S = 64) or of state l
-// (S <= 32) of one tile, so a stage is one butterfly per lane: the metrics of
-// the two predecessors (Eq. 3) come from their lanes by shuffle, the
-// decisions (Eq. 4) of all states by ballot, a 64-bit word per stage.
-// Metrics are 32-bit and compared by signed
-// difference, so they may wrap; decisions and the traceback start (argmax,
-// ties to the lowest state, Alg. 2) are those of unbounded integers.  The
-// decision words of the window stay in the warp's shared memory, so windows
-// are limited to kWarpSmemStages stages.
+// l holds the path metrics of states 2l and 2l + 1 (S = 64) or of state l
+// (S <= 32) of one tile: the two predecessors 2s, 2s + 1 (mod S) of a state
+// s (Eq. 3) then sit in one lane and come over by shuffle, and the decisions
+// (Eq. 4) of all states are gathered by ballot into a 64-bit word per stage.
+// Metrics are 32-bit integers far from overflow (a window of at most
+// kWarpSmemStages stages moves them by at most 127 beta per stage), so
+// decisions and the traceback start (argmax, ties to the lowest state,
+// Alg. 2) are those of unbounded integers.  The decision words of the window
+// stay in the warp's shared memory, so windows are limited to
+// kWarpSmemStages stages.
 #pragma once
 #include "vit_acs.cuh"
 
@@ -38,65 +39,85 @@ __device__ __forceinline__ uint32_t warp_llr_word(const int8_t* llr, int i, int 
   return w;
 }
 
+// Spreads the 32 bits of x to the even bit positions of a 64-bit word.
+__device__ __forceinline__ uint64_t spread_even(uint32_t x) {
+  uint64_t v = x;
+  v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+  v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+  v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  v = (v | (v << 1)) & 0x5555555555555555ull;
+  return v;
+}
+
 // One trellis stage (Eq. 3, Eq. 4) of the warp's tile: `pk` holds the
-// stage's LLR bytes, m the lane's metrics; returns the two ballot words.
+// stage's LLR bytes, m the lane's metrics (states R*lane + r); returns the
+// ballot of each register's decisions.  Both predecessors 2s, 2s+1 (mod S)
+// of state s sit in one lane: registers 0 and 1 of lane s mod 32 when
+// R = 2, register 0 of lanes 2s and 2s+1 (mod S) when R = 1.  The metrics
+// stay far from 2^31 (windows of at most kWarpSmemStages stages), so the
+// survivor is a plain signed max and the decision compare is off the
+// metrics' dependency chain.
 template <class C>
-__device__ __forceinline__ void warp_stage(uint32_t (&m)[C::S > 32 ? 2 : 1], uint32_t pk, int src0, int src1,
-                                           int reg, bool live, const uint32_t (&cA)[C::S > 32 ? 2 : 1],
+__device__ __forceinline__ void warp_stage(int (&m)[C::S > 32 ? 2 : 1], uint32_t pk, int lane, bool live,
+                                           const uint32_t (&cA)[C::S > 32 ? 2 : 1],
                                            const uint32_t (&cB)[C::S > 32 ? 2 : 1], uint32_t (&bal)[2]) {
-  constexpr int R = C::S > 32 ? 2 : 1;
+  constexpr int S = C::S;
+  constexpr int R = S > 32 ? 2 : 1;
   int l[C::BETA];
 #pragma unroll
   for (int b = 0; b < C::BETA; b++) l[b] = (int)(int8_t)(uint8_t)(pk >> (8 * b));
-  // metrics of the two predecessors: register `reg` of lanes src0, src1
-  uint32_t q0 = __shfl_sync(0xffffffffu, m[0], src0), q1 = __shfl_sync(0xffffffffu, m[0], src1);
+  int q0[R], q1[R];
   if constexpr (R == 2) {
-    const uint32_t u0 = __shfl_sync(0xffffffffu, m[1], src0), u1 = __shfl_sync(0xffffffffu, m[1], src1);
-    q0 = reg ? u0 : q0;
-    q1 = reg ? u1 : q1;
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      const int src = (2 * lane + r) & 31;
+      q0[r] = __shfl_sync(0xffffffffu, m[0], src);
+      q1[r] = __shfl_sync(0xffffffffu, m[1], src);
+    }
+  } else {
+    q0[0] = __shfl_sync(0xffffffffu, m[0], (2 * lane) & (S - 1));
+    q1[0] = __shfl_sync(0xffffffffu, m[0], (2 * lane + 1) & (S - 1));
   }
   bal[1] = 0u;
 #pragma unroll
   for (int r = 0; r < R; r++) {
-    const uint32_t x0 = q0 + (uint32_t)warp_delta<C>(l, cA[r]), x1 = q1 + (uint32_t)warp_delta<C>(l, cB[r]);
-    const bool d = live && (int)(x1 - x0) > 0;  // ties keep the even predecessor
-    bal[r] = __ballot_sync(0xffffffffu, d);
-    m[r] = d ? x1 : x0;
+    const int x0 = q0[r] + warp_delta<C>(l, cA[r]), x1 = q1[r] + warp_delta<C>(l, cB[r]);
+    bal[r] = __ballot_sync(0xffffffffu, live && x1 > x0);  // ties keep the even predecessor
+    m[r] = x1 > x0 ? x1 : x0;
   }
 }
 
 // Decodes tile `h` (window [t0, t1), emitted [e0, e1)) with the calling warp.
 // dec: the tile's decision words, one 64-bit word per stage of the window
-// (shared memory).  The window's LLRs arrive 32 stages at a time (lane l
-// loads stage i0 + l, one block ahead) and each stage takes its bytes by
-// shuffle, off the metrics' dependency chain; lane l keeps the decision
-// word of stage i0 + l and the warp stores a block's words together.
+// (shared memory, bit s = state s).  The window's LLRs arrive 32 stages at a
+// time (lane l loads stage i0 + l, one block ahead) and each stage takes its
+// bytes by shuffle, off the metrics' dependency chain; lane l keeps the
+// ballots of stage i0 + l and the warp stores a block's words together.
 template <class C>
 __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int lane) {
   static_assert(C::S <= 64 && C::BETA <= 4, "states of one tile over the 32 lanes; LLR bytes in one word");
   constexpr int S = C::S;
-  constexpr int R = S > 32 ? 2 : 1;  // states per lane
+  constexpr int R = S > 32 ? 2 : 1;  // states per lane: R * lane + r
   const int L = (int)(h.t1 - h.t0);
-  // lane l holds states l + 32 r; state j's predecessors are 2j mod S and
-  // 2j+1 mod S, reached by the branches R0 = 2j and R0 + 1 (the two states
-  // of a lane share their predecessors: a butterfly)
-  uint32_t m[R];
+  int m[R];
+  uint32_t cA[R], cB[R];  // output patterns of the branches from 2s and 2s + 1
 #pragma unroll
   for (int r = 0; r < R; r++) {
-    const int j = lane + 32 * r;
-    m[r] = (h.known && j != 0) ? 0u - M : 0u;
+    const int j = R * lane + r;
+    m[r] = (h.known && j != 0) ? -(int)M : 0;
+    cA[r] = C::aout(2u * (uint32_t)j);
+    cB[r] = C::aout(2u * (uint32_t)j + 1u);
   }
-  const int p0 = (2 * lane) & (S - 1);
-  const int src0 = p0 & 31, src1 = (p0 + 1) & 31, reg = p0 >> 5;
-  uint32_t cA[R], cB[R];
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const uint32_t j = (uint32_t)(lane + 32 * r);
-    cA[r] = C::aout(2u * j);
-    cB[r] = C::aout(2u * j + 1u);
-  }
-  const bool live = lane < S;
+  const bool live = R * lane < S;
   const int8_t* llr = h.llr + h.t0 * C::BETA;
+  // the stage word of lane l's kept ballots, bit s = state s
+  auto word = [](uint32_t kA, uint32_t kB) -> uint64_t {
+    if constexpr (R == 2)
+      return spread_even(kA) | (spread_even(kB) << 1);
+    else
+      return (uint64_t)kA;
+  };
   uint32_t nxt = warp_llr_word<C>(llr, lane, L);
   int i0 = 0;
   for (; i0 + 32 <= L; i0 += 32) {  // whole blocks of 32 stages
@@ -106,40 +127,40 @@ __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int l
 #pragma unroll
     for (int k = 0; k < 32; k++) {
       uint32_t bal[2];
-      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), src0, src1, reg, live, cA, cB, bal);
+      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), lane, live, cA, cB, bal);
       kA = lane == k ? bal[0] : kA;
       kB = lane == k ? bal[1] : kB;
     }
-    dec[i0 + lane] = (uint64_t)kA | ((uint64_t)kB << 32);
+    dec[i0 + lane] = word(kA, kB);
   }
   if (i0 < L) {  // the last, partial block
     const uint32_t cur = nxt;
     uint32_t kA = 0u, kB = 0u;
     for (int k = 0; k < L - i0; k++) {
       uint32_t bal[2];
-      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), src0, src1, reg, live, cA, cB, bal);
+      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), lane, live, cA, cB, bal);
       kA = lane == k ? bal[0] : kA;
       kB = lane == k ? bal[1] : kB;
     }
-    if (i0 + lane < L) dec[i0 + lane] = (uint64_t)kA | ((uint64_t)kB << 32);
+    if (i0 + lane < L) dec[i0 + lane] = word(kA, kB);
   }
-  // traceback start: argmax (ties to the lowest state) relative to state 0
-  int best = lane;
-  uint32_t bv = m[0];
+  // traceback start: argmax, ties to the lowest state
+  int best = R * lane, bv = m[0];
   if constexpr (R == 2) {
-    if ((int)(m[1] - m[0]) > 0) {
-      best = lane + 32;
+    if (m[1] > m[0]) {
+      best = R * lane + 1;
       bv = m[1];
     }
   }
-  const uint32_t ref = __shfl_sync(0xffffffffu, m[0], 0);
-  int rel = live ? (int)(bv - ref) : (-2147483647 - 1);
-  if (!live) best = S;
+  if (!live) {
+    best = S;
+    bv = -2147483647 - 1;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const int orel = __shfl_xor_sync(0xffffffffu, rel, o), ob = __shfl_xor_sync(0xffffffffu, best, o);
-    if (orel > rel || (orel == rel && ob < best)) {
-      rel = orel;
+    const int ov = __shfl_xor_sync(0xffffffffu, bv, o), ob = __shfl_xor_sync(0xffffffffu, best, o);
+    if (ov > bv || (ov == bv && ob < best)) {
+      bv = ov;
       best = ob;
     }
   }
