@@ -2,8 +2,9 @@
 host memory, copied in, decoded and copied back in chunks on plan-owned
 streams.  Every output is compared with the oracle bit for bit: long
 streams cut into many chunks, mixed codes with terminated and punctured
-frames, chunk counts from 1 to 64, graph replay, and a second run after the
-host inputs changed (the copies happen every run)."""
+frames, whole-frame tiles (f = 0), a parallel-traceback group, chunk counts
+from 1 to 64, graph replay, and a second run after the host inputs changed
+(the copies happen every run)."""
 import numpy as np
 import pytest
 import torch
@@ -136,3 +137,29 @@ def test_host_batch_rejects_device_and_pageable_buffers(vit):
         h = ctypes.c_void_p()
         assert L.vit_batch_plan(ctypes.byref(h), arr, 1, vit.BATCH_HOST) == -1
         assert b"page-locked" in L.vit_last_error()
+
+
+def test_host_batch_whole_frames_and_parallel_traceback(vit):
+    """Frames decoded whole (f = 0: one tile each, full-frame Viterbi) next to
+    a parallel-traceback group (f0 = 32, random starts) in one host-staged
+    batch."""
+    specs, checks = [], []
+    whole = vit.Code(*K7, f=0, v=0, mode=vit.TERMINATED)
+    for i, n in enumerate((70, 1030, 4102, 8000)):
+        s = synth.make_stream(_enc(K7), 2, n, 3.0, seed=40 + i, tail=6)
+        want, _ = oracle.viterbi_full(*K7, s.llr, oracle.TERMINATED)
+        out = torch.full(((n - 6 + 7) // 8,), 0xAA, dtype=torch.uint8).pin_memory()
+        specs.append((whole, _pinned(s.llr, torch.int8), n, vit.TERMINATED, out))
+        checks.append((out, n - 6, np.asarray(want)[: n - 6]))
+    pt = vit.Code(*K7, f=1024, v=48, pt_f0=32, pt_rule=vit.PT_RANDOM, pt_seed=9)
+    for i, n in enumerate((30000, 12345)):
+        s = synth.make_stream(_enc(K7), 2, n, 2.5, seed=50 + i)
+        want = oracle.viterbi_blocked_pt(*K7, s.llr, 1024, 48, 48, 32, start=oracle.PT_RANDOM, seed=9)
+        out = torch.full(((n + 7) // 8,), 0x55, dtype=torch.uint8).pin_memory()
+        specs.append((pt, _pinned(s.llr, torch.int8), n, vit.STREAM, out))
+        checks.append((out, n, want))
+    b = vit.Batch(specs, graph=True, host=True, chunks=5)
+    b.run()
+    torch.cuda.synchronize()
+    for k, (o, nout, want) in enumerate(checks):
+        np.testing.assert_array_equal(synth.unpack_bits(o.numpy(), nout), want, err_msg=f"frame {k}")
