@@ -14,7 +14,8 @@
 // The forward pass is the tile decoder's (byte loads, both tiles of a lane
 // in the two 16-bit fields); after every stage at which a subframe of either
 // tile starts its traceback, the lane records that tile's argmax state.  The
-// traceback then runs per tile and per subframe.
+// traceback then runs per subframe, both tiles of the lane together when
+// their subframes line up.
 #pragma once
 #include "vit_acs.cuh"
 
@@ -95,37 +96,52 @@ VIT_HD int pt_first_capture(const Half& h, int64_t e1f, int64_t nsub, int64_t v2
   return h.start + (int)(sf.u - h.t0);
 }
 
-// Traceback of tile h, one subframe at a time (last first).
+// Start state of subframe sf of tile hw (k: its index): the tile's usual
+// start when sf is traced from the window's last stage, else the recorded
+// argmax (rule 0) or the top K-1 bits of SplitMix64 output u (rule 1).
 template <class C>
-VIT_HD void pt_traceback(const Half& hw, int h, int64_t e1f, int64_t nsub, int64_t v2, const PtParams& pt,
-                         const uint8_t* st, Slab sl) {
-  for (int64_t k = nsub - 1; k >= 0; k--) {
-    const Subframe sf = pt_subframe(hw, e1f, pt.f0, v2, k);
-    if (k > 0) {  // the next subframe's survivor words, into L2
-      const Subframe nf = pt_subframe(hw, e1f, pt.f0, v2, k - 1);
-      slab_prefetch_l2(sl, hw.start + (int)(nf.s0 - hw.t0), (int)(nf.u - nf.s0 + 1));
-    }
-    uint32_t j;
-    if (sf.u == hw.t1 - 1)
-      j = hw.end_zero ? 0u : (uint32_t)st[k];
-    else if (pt.rule == 0)
-      j = (uint32_t)st[k];
-    else
-      j = (uint32_t)(splitmix64_output(pt.seed, (uint64_t)sf.u) >> (64 - C::KM1));
-    const int64_t emit_hi = sf.s1 < hw.e1 ? sf.s1 : hw.e1;
-    uint32_t acc = 0u;
-    for (int64_t t = sf.u; t >= sf.s0; t--) {
-      uint32_t w[C::WORDS];
-      load_words<C>(sl, hw.start + (int)(t - hw.t0), w);
-      const uint32_t d = tb_decision<C>(w, j, h);
-      if (t < emit_hi) {
-        acc |= ((j >> (C::K - 2)) & 1u) << (t & 7);
-        if ((t & 7) == 0 || t == sf.s0) {
-          store_byte(hw.out + (t >> 3), acc);
-          acc = 0u;
-        }
+VIT_HD uint32_t pt_start(const Half& hw, const Subframe& sf, int64_t k, const PtParams& pt, const uint8_t* st) {
+  if (sf.u == hw.t1 - 1) return hw.end_zero ? 0u : (uint32_t)st[k];
+  if (pt.rule == 0) return (uint32_t)st[k];
+  return (uint32_t)(splitmix64_output(pt.seed, (uint64_t)sf.u) >> (64 - C::KM1));
+}
+
+// Traceback of a lane's tiles, one subframe at a time (last first).  Each
+// subframe is the tile decoder's traceback (traceback_pair) over iterations
+// up to its stage u, emitting its own stages only.  The two tiles go
+// together when their subframes cover the same iterations (every interior
+// tile pair), else one after the other.
+template <class C>
+VIT_HD void pt_traceback_pair(const Half (&hw)[2], const int64_t (&e1f)[2], const int64_t (&nsub)[2], int64_t v2,
+                              const PtParams& pt, uint8_t* const (&st)[2], Slab sl) {
+  const bool paired = hw[0].active && hw[1].active && nsub[0] == nsub[1] && hw[0].start == hw[1].start &&
+                      hw[0].e0 - hw[0].t0 == hw[1].e0 - hw[1].t0 && hw[0].t1 - hw[0].t0 == hw[1].t1 - hw[1].t0 &&
+                      e1f[0] - hw[0].e0 == e1f[1] - hw[1].e0 && hw[0].e1 - hw[0].e0 == hw[1].e1 - hw[1].e0;
+  for (int pass = 0; pass < (paired ? 1 : 2); pass++) {
+    const int lead = paired ? 0 : pass;  // the tile whose geometry drives this pass
+    if (!hw[lead].active) continue;
+    for (int64_t k = nsub[lead] - 1; k >= 0; k--) {
+      const Subframe sf = pt_subframe(hw[lead], e1f[lead], pt.f0, v2, k);
+      if (k > 0) {  // the next subframe's survivor words, into L2
+        const Subframe nf = pt_subframe(hw[lead], e1f[lead], pt.f0, v2, k - 1);
+        slab_prefetch_l2(sl, hw[lead].start + (int)(nf.s0 - hw[lead].t0), (int)(nf.u - nf.s0 + 1));
       }
-      j = (2u * j + d) & (uint32_t)(C::S - 1);
+      Half hs[2];
+      int s0[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        hs[h] = hw[h];
+        s0[h] = 0;
+        if (!(paired || h == lead)) {
+          hs[h].active = 0;
+          continue;
+        }
+        const Subframe sh = pt_subframe(hw[h], e1f[h], pt.f0, v2, k);
+        hs[h].e0 = sh.s0;
+        hs[h].e1 = sh.s1 < hw[h].e1 ? sh.s1 : hw[h].e1;
+        s0[h] = (int)pt_start<C>(hw[h], sh, k, pt, st[h]);
+      }
+      traceback_pair<C>(hs, hw[lead].start + (int)(sf.u - hw[lead].t0) + 1, s0, sl);
     }
   }
 }
@@ -168,9 +184,7 @@ VIT_HD void decode_pair_pt(const Half (&hw)[2], const int64_t (&e1f)[2], int Lw,
     if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
     cur = nxt;
   }
-#pragma unroll
-  for (int h = 0; h < 2; h++)
-    if (hw[h].active) pt_traceback<C>(hw[h], h, e1f[h], nsub[h], v2, pt, st[h], sl);
+  pt_traceback_pair<C>(hw, e1f, nsub, v2, pt, st, sl);
 }
 
 }  // namespace vit
