@@ -19,7 +19,14 @@ __global__ void __maxnreg__(kMaxRegs) decode_tiles_pt_kernel(const KArgs a) {
   uint8_t* const st[2] = {hw[0].active ? a.pt_states + gt[0] * a.pt_nsub : nullptr,
                           hw[1].active ? a.pt_states + gt[1] * a.pt_nsub : nullptr};
   const PtParams pt{a.pt_f0, a.pt_rule, a.pt_seed};
-  decode_pair_pt<C>(hw, e1f, Lw, mu, a.M, sl, a.tl.v2, pt, st);
+  // word loads need every active tile's groups to start on 4-byte boundaries
+  bool aligned = true;
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+    if (hw[h].active)
+      aligned = aligned && ((reinterpret_cast<uintptr_t>(hw[h].llr) +
+                             (uintptr_t)((hw[h].t0 - hw[h].start) * C::BETA)) % 4u == 0u);
+  decode_pair_pt<C>(hw, e1f, Lw, mu, a.M, sl, a.tl.v2, pt, st, __all_sync(0xffffffffu, aligned));
 }
 
 template <class C>

@@ -11,8 +11,9 @@
 // path metrics, recorded during the forward pass (rule 0), or the top K-1
 // bits of SplitMix64 output u under the caller's seed (rule 1).
 //
-// The forward pass is the tile decoder's (byte loads, both tiles of a lane
-// in the two 16-bit fields); after every stage at which a subframe of either
+// The forward pass is the tile decoder's (32-bit LLR word loads once every
+// window of the warp has started, both tiles of a lane in the two 16-bit
+// fields); after every stage at which a subframe of either
 // tile starts its traceback, the lane records that tile's argmax state.  The
 // traceback then runs per subframe, both tiles of the lane together when
 // their subframes line up.
@@ -147,10 +148,12 @@ VIT_HD void pt_traceback_pair(const Half (&hw)[2], const int64_t (&e1f)[2], cons
 }
 
 // Decodes the two tiles of one lane with the parallel traceback.  st[h]:
-// the tile's recorded start states (one byte per subframe).
+// the tile's recorded start states (one byte per subframe); words_ok: the
+// warp's tiles allow the 32-bit LLR word loads of the tile decoder (groups
+// before every window has started still use masked byte loads).
 template <class C>
 VIT_HD void decode_pair_pt(const Half (&hw)[2], const int64_t (&e1f)[2], int Lw, int masked_until, uint32_t M,
-                           Slab sl, int64_t v2, const PtParams& pt, uint8_t* const (&st)[2]) {
+                           Slab sl, int64_t v2, const PtParams& pt, uint8_t* const (&st)[2], bool words_ok) {
   static_assert(C::G == 1 && C::U == 2, "one lane per tile pair");
   uint32_t ma[C::NS], mb[C::NS];
 #pragma unroll
@@ -165,24 +168,62 @@ VIT_HD void decode_pair_pt(const Half (&hw)[2], const int64_t (&e1f)[2], int Lw,
     nsub[h] = hw[h].active && e1f[h] > hw[h].e0 ? (e1f[h] - hw[h].e0 + pt.f0 - 1) / pt.f0 : 0;
     next[h] = pt_first_capture(hw[h], e1f[h], nsub[h], v2, pt, Lw);
   }
+  // the argmax capture after the stage at iteration i (metrics m)
+  auto capture = [&](const uint32_t (&m)[C::NS], int i) {
+    if (next[0] == i || next[1] == i) pt_capture<C>(m, i, hw, e1f, nsub, v2, pt, st, next, k);
+  };
   const int ngroups = Lw / C::U;
-  LlrGroup<C> cur, nxt;
-  load_group<C>(hw, 0, cur);
-  for (int g = 0; g < ngroups; g++) {
-    const int i0 = g * C::U;
-    if (g + 1 < ngroups) {
-      if (i0 + C::U < masked_until)
-        load_group<C>(hw, i0 + C::U, nxt);
-      else
-        load_group_fast<C>(hw, i0 + C::U, nxt);
+  bool words = false;
+  if constexpr (kWordLoads<C>) words = words_ok;
+  if (words) {
+    if constexpr (kWordLoads<C>) {
+      int g = 0;
+      for (; g < ngroups && g * C::U < masked_until; g++) {  // masked byte loads
+        const int i0 = g * C::U;
+        LlrGroup<C> lg;
+        load_group<C>(hw, i0, lg);
+        fwd_stage<C>(ma, mb, hw, i0, true, M, lg.v[0], sl);
+        capture(mb, i0);
+        fwd_stage<C>(mb, ma, hw, i0 + 1, true, M, lg.v[1], sl);
+        capture(ma, i0 + 1);
+        if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
+      }
+      constexpr int NW = C::U * C::BETA / 4;
+      uint32_t wc[2][NW], wn[2][NW];
+      if (g < ngroups) load_group_words<C>(hw, g * C::U, wc);
+      for (; g < ngroups; g++) {
+        const int i0 = g * C::U;
+        if (g + 1 < ngroups) load_group_words<C>(hw, i0 + C::U, wn);  // prefetch the next group
+        fwd_stage_words<C, 0>(ma, mb, i0, wc, sl);
+        capture(mb, i0);
+        fwd_stage_words<C, 1>(mb, ma, i0 + 1, wc, sl);
+        capture(ma, i0 + 1);
+        if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+          for (int q = 0; q < NW; q++) wc[h][q] = wn[h][q];
+      }
     }
-    const bool masked = i0 < masked_until;
-    fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl);
-    if (next[0] == i0 || next[1] == i0) pt_capture<C>(mb, i0, hw, e1f, nsub, v2, pt, st, next, k);
-    fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl);
-    if (next[0] == i0 + 1 || next[1] == i0 + 1) pt_capture<C>(ma, i0 + 1, hw, e1f, nsub, v2, pt, st, next, k);
-    if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
-    cur = nxt;
+  } else {
+    LlrGroup<C> cur, nxt;
+    load_group<C>(hw, 0, cur);
+    for (int g = 0; g < ngroups; g++) {
+      const int i0 = g * C::U;
+      if (g + 1 < ngroups) {
+        if (i0 + C::U < masked_until)
+          load_group<C>(hw, i0 + C::U, nxt);
+        else
+          load_group_fast<C>(hw, i0 + C::U, nxt);
+      }
+      const bool masked = i0 < masked_until;
+      fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl);
+      capture(mb, i0);
+      fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl);
+      capture(ma, i0 + 1);
+      if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
+      cur = nxt;
+    }
   }
   pt_traceback_pair<C>(hw, e1f, nsub, v2, pt, st, sl);
 }

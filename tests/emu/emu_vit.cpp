@@ -84,12 +84,18 @@ static int emu_pt(const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v
           if (hw[l][h].start + 1 > masked_until) masked_until = hw[l][h].start + 1;
         }
     std::vector<uint32_t> slab((size_t)Lw * C::WORDS);
+    bool words = true;  // the kernel's warp-wide alignment vote
+    for (int l = 0; l < 32; l++)
+      for (int h = 0; h < 2; h++)
+        if (hw[l][h].active)
+          words = words && ((reinterpret_cast<uintptr_t>(hw[l][h].llr) +
+                             (uintptr_t)((hw[l][h].t0 - hw[l][h].start) * C::BETA)) % 4u == 0u);
     for (int l = 0; l < 32; l++) {
       if (!hw[l][0].active && !hw[l][1].active) continue;
       Slab sl{slab.data(), C::WORDS};
       uint8_t* const st[2] = {states.data() + (task * 64 + 2 * l) * nsub,
                               states.data() + (task * 64 + 2 * l + 1) * nsub};
-      decode_pair_pt<C>(hw[l], e1f[l], Lw, masked_until, (uint32_t)M, sl, v2, pt, st);
+      decode_pair_pt<C>(hw[l], e1f[l], Lw, masked_until, (uint32_t)M, sl, v2, pt, st, words);
     }
   }
   return 0;
