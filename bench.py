@@ -34,9 +34,10 @@ EBN0 = [0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0]
 WORKLOAD = ("stream K=7 r1/2 (171,133 octal) f=1024 v1=v2=48, 7 streams x 2^24 info bits, "
             "Eb/N0 0..6 dB, int8 LLRs x16")
 METRIC = "decoded Mbit/s K=7 r1/2 int8, batched vs per-frame, 1 GB300; % ALU/HBM roofline"
-SM_COUNT = 152
-LANES_PER_SM_CLK = 4 * 32      # 4 SM sub-partitions x 32 lanes issue full-rate integer ops
-OPS_PER_LANE = 2               # two 16-bit path metrics per 32-bit lane (packed max.u16x2 / IADD3)
+# algorithmic int16 operations one lane performs with one instruction of each
+# class: a 32-bit add of two packed 16-bit metrics is two adds, max.u16x2 is a
+# compare and a select on each of its two fields
+OPS_PER_LANE_INSTR = {"iadd": 2, "imad": 2, "vmax16": 4}
 
 
 def _peaks():
@@ -46,6 +47,30 @@ def _peaks():
         return float(p.get("sm_max_mhz", 2070.0)), float(p.get("hbm_gbs", 6800.0)), "measured"
     except OSError:
         return 2070.0, 6800.0, "fallback"
+
+
+def alu_peak_leg(vit, device):
+    """Measured instruction rates of the decoder's integer classes
+    (vit_probe_rate: 32 warps per SM, 8 independent chain pairs per thread),
+    in warp instructions per SM clock per SM, and the packed-int16 peak they
+    imply: max over classes of rate x 32 lanes x algorithmic ops per lane."""
+    rates, sms = {}, None
+    for k in ("iadd", "imad", "vmax16", "prmt", "lop3"):
+        r, _, sms = vit.probe_rate(k, 4, 8, 2000, device=device)
+        rates[k] = r
+    best = max(OPS_PER_LANE_INSTR, key=lambda k: rates[k] * 32 * OPS_PER_LANE_INSTR[k])
+    per_clk_sm = rates[best] * 32 * OPS_PER_LANE_INSTR[best]
+    return {"warp_instr_per_clk_sm": rates, "sms": sms, "int16_ops_per_clk_sm": per_clk_sm, "peak_class": best}
+
+
+def fp_peak_leg(vit, device):
+    """Measured FP32 and MUFU rates (vit_probe_rate), warp instructions per
+    SM clock per SM: the denominators of the path-metric kernels."""
+    out = {}
+    for k in ("fadd", "fmax", "ex2", "lg2"):
+        r, _, sms = vit.probe_rate(k, 4, 8, 1000, device=device)
+        out[k] = r
+    return out
 
 
 def _kernel_source_sha() -> str:
@@ -655,7 +680,8 @@ def main():
 
     sm_max, hbm_gbs, peak_src = _peaks()
     ops = algorithmic_ops_per_step()
-    peak_tops = SM_COUNT * LANES_PER_SM_CLK * OPS_PER_LANE * sm_max * 1e6 / 1e12
+    probe = alu_peak_leg(vit, dev)
+    peak_tops = probe["int16_ops_per_clk_sm"] * probe["sms"] * sm_max * 1e6 / 1e12
     achieved_tops = ops / (launch_ms * 1e-3) / 1e12
     clocks = clk.summary()
     traffic = _traffic_per_launch()
@@ -676,7 +702,12 @@ def main():
                                "ms_per_step": seq_ms, "how": "H2D, decode, D2H in turn on one stream"}},
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
                      "frac": achieved_tops / peak_tops, "traffic": traffic,
-                     "peak_source": f"{SM_COUNT} SMs x 128 lanes x 2 int16 ops x {sm_max:.0f} MHz ({peak_src} max clock)",
+                     "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
+                     "peak_source": (f"alu_peak leg (vit_probe_rate): {probe['peak_class']} at "
+                                     f"{probe['warp_instr_per_clk_sm'][probe['peak_class']]:.3f} warp-instr/clk/SM x 32 "
+                                     f"lanes x {OPS_PER_LANE_INSTR[probe['peak_class']]} int16 ops x {probe['sms']} SMs "
+                                     f"x {sm_max:.0f} MHz ({peak_src} max clock)"),
+                     "alu_peak": probe,
                      "kernel": "decode_tiles_kernel<K=7,beta=2>", "launch_ms": launch_ms,
                      "hbm_alg_gbs": alg_bytes / (launch_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_gbs},
         "clocks": clocks,
@@ -688,6 +719,7 @@ def main():
         "ber_6db": ber6,
     }
     if clocks.get("sm_mhz"):
+        line["roofline"]["peak_at_sampled_clock"] = peak_tops * clocks["sm_mhz"] / sm_max
         line["roofline"]["frac_at_sampled_clock"] = achieved_tops / (peak_tops * clocks["sm_mhz"] / sm_max)
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
         v, cores, sample, v1 = cpu_oracle_rate()

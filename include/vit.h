@@ -143,10 +143,13 @@ int vit_decode(const vit_code* code, const int8_t* llr, int64_t n, uint8_t* bits
  * array compiled into the library (every GPU that loads it holds the array
  * until exit); frames whose vit_decode_workspace(code, n) exceeds 16 MiB are
  * rejected with VIT_EINVAL.  The first call on each device (with that device
- * current) looks up the array's address, so make it before any stream
- * capture.  All calls on a device share the array: calls whose work overlaps
- * on the GPU (e.g. on different streams) race and must be serialised by the
- * caller.  llr, n and bits_out are as for vit_decode_ws.
+ * current) looks up the array's address and caches it, so make it before any
+ * stream capture; after a cudaDeviceReset of that device the cached address
+ * is stale and this entry point must not be used there again.  The stream
+ * must belong to the current device (VIT_EINVAL otherwise).  All calls on a
+ * device share the array: calls whose work overlaps on the GPU (e.g. on
+ * different streams) race and must be serialised by the caller.  llr, n and
+ * bits_out are as for vit_decode_ws.
  */
 int vit_decode_noalloc(const vit_code* code, const int8_t* llr, int64_t n, uint8_t* bits_out, vit_stream_t stream);
 

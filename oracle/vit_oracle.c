@@ -19,7 +19,7 @@
  * plus two quantities the paper does not define (best-path metric and its
  * temperature log-sum-exp relaxation, with gradients) and brute-force ML.
  *
- * Conventions where the paper is silent (each is listed in the design doc):
+ * Conventions where the paper is silent (each is a reading of the paper):
  *  - Generator g_b is a K-bit word; bit K-1 is the tap on the current input
  *    (Eq. 1 pairs g_{K-1} with in_t).  Register word R_t = in_t*2^(K-1) + s_t.
  *  - State s_t = sum_{m=1}^{K-1} in_{t-m} 2^{K-1-m} (newest input = MSB).

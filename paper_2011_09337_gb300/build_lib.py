@@ -3,6 +3,12 @@
 Every ``csrc/*.cu`` file is compiled for sm_103a only, in parallel, then
 linked into ``paper_2011_09337_gb300/_build/libvit.so``.  Objects are rebuilt
 when a source or header is newer than them.
+
+Development aid: ``VIT_BUILD_SKIP`` (comma-separated file stems, e.g.
+``vit_codes_k9,vit_codes_k9_bytes,vit_mixed``) leaves those translation
+units out of the library, to shorten rebuilds while iterating on other
+kernels.  Codes whose kernels are left out are then served by the generic
+decoders.  The default build compiles everything.
 """
 from __future__ import annotations
 
@@ -34,9 +40,22 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _members_changed(objs: list[str]) -> bool:
+    """True when the library was linked from another set of objects."""
+    listing = LIB + ".objs"
+    want = "\n".join(os.path.basename(o) for o in objs)
+    try:
+        with open(listing) as fh:
+            return fh.read() != want
+    except OSError:
+        return True
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    skip = {x.strip() for x in os.environ.get("VIT_BUILD_SKIP", "").split(",") if x.strip()}
+    srcs = sorted(p for p in glob.glob(os.path.join(CSRC, "*.cu"))
+                  if os.path.basename(p)[:-3] not in skip)
     hdrs = _headers()
     objs = []
     jobs = []
@@ -62,13 +81,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
             for msg in ex.map(compile_one, jobs):
                 if verbose and msg:
                     sys.stderr.write(msg)
-    if force or jobs or _stale(LIB, objs):
+    if force or jobs or _stale(LIB, objs) or _members_changed(objs):
         tmp = LIB + f".{os.getpid()}.tmp"
         cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp, LIB)
+        with open(LIB + ".objs", "w") as fh:
+            fh.write("\n".join(os.path.basename(o) for o in objs))
     return LIB
 
 

@@ -11,10 +11,15 @@
 // The array is kVitNoallocScratchBytes (16 MiB) per GPU, held by every device
 // that loads the library until the process exits.  Its device address is
 // looked up once per device (cudaGetSymbolAddress, on the first call made
-// with that device current) and cached.  Every call on a device shares the
-// array; the decoder writes each scratch word before reading it in the same
-// launch, so nothing needs clearing, but calls whose kernels overlap on the
-// GPU (for example on two streams) race on it.
+// with that device current) and cached; a cudaDeviceReset of that device
+// rebuilds the module and invalidates the cached address, so the entry point
+// must not be used on a device after it has been reset.  The caller's stream
+// must belong to the current device (checked: the scratch address is the
+// current device's).  Every call on a device shares the array; the decoder
+// writes each scratch word before reading it in the same launch (survivor
+// words of a stage before the traceback reads them, de-punctured LLRs before
+// the decode launch reads them), so nothing needs clearing, but calls whose
+// kernels overlap on the GPU (for example on two streams) race on it.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,6 +72,12 @@ int vit_decode_noalloc(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
                           "frame needs %zu bytes of decoder scratch; the allocation-free entry point has %zu "
                           "(use vit_decode_ws or shorter frames)",
                           need, kVitNoallocScratchBytes);
+  int cur = -1, sdev = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e == cudaSuccess) e = cudaStreamGetDevice((cudaStream_t)stream, &sdev);
+  if (e != cudaSuccess) return vit::set_error(VIT_ECUDA, "stream device query: %s", cudaGetErrorString(e));
+  if (sdev != cur)
+    return vit::set_error(VIT_EINVAL, "stream belongs to device %d but device %d is current", sdev, cur);
   void* ws = nullptr;
   if (int r = scratch_address(&ws)) return r;
   return vit::decode_into(c, llr, n, bits_out, ws, kVitNoallocScratchBytes, (cudaStream_t)stream);

@@ -65,9 +65,32 @@ def default_candidates(K: int):
     return [(f, v) for f in fs for v in vs if not (f == 0 and v != vs[0])]
 
 
-def tune(frames, codes, candidates=None, max_disagree: float = 2e-4, warps_options=(2, 4, 8), reps: int = 3):
+def pick(rows, max_disagree: float):
+    """The fastest timed tiling whose disagreement with the full-frame decode
+    is at most ``max_disagree`` (rows: dicts with f, v, ms, disagree), or
+    None when no row qualifies."""
+    best = None
+    for r in rows:
+        if r["disagree"] <= max_disagree and (best is None or r["ms"] < best.ms):
+            best = Choice(r["f"], r["v"], r["ms"], r["disagree"])
+    return best
+
+
+def _make_code(K, beta, polys, f, v, mode):
+    return vit.Code(K, beta, polys, f=f, v=v, mode=mode)
+
+
+def tune(frames, codes, candidates=None, max_disagree: float = 2e-4, warps_options=(2, 4, 8), reps: int = 3,
+         runner=None, make_code=None):
     """frames: list of (code_index, llr CUDA int8 tensor, n, mode);
-    codes: list of (K, beta, polys).  Returns ({code_index: Choice}, warps, report)."""
+    codes: list of (K, beta, polys).  Returns ({code_index: Choice}, warps, report).
+
+    ``runner(frames, code_map, warps=.., reps=..) -> (ms, packed bits)`` and
+    ``make_code(K, beta, polys, f, v, mode)`` default to timed, graph-captured
+    batch runs of the library and ``vit.Code``; they are parameters so that
+    the selection logic can be exercised with a cost table."""
+    runner = runner or _run
+    make_code = make_code or _make_code
     chosen = {}
     report = {}
     for ci, (K, beta, polys) in enumerate(codes):
@@ -78,27 +101,25 @@ def tune(frames, codes, candidates=None, max_disagree: float = 2e-4, warps_optio
         mode = modes.pop() if len(modes) == 1 else vit.STREAM
 
         def code_for(f, v):
-            return {ci: vit.Code(K, beta, polys, f=f, v=v, mode=mode)}
+            return {ci: make_code(K, beta, polys, f, v, mode)}
 
-        ref_code = code_for(0, 0)
-        _, ref_out = _run(sub, ref_code, reps=1)
-        best = None
+        _, ref_out = runner(sub, code_for(0, 0), reps=1)
         rows = []
         for f, v in (candidates or default_candidates(K)):
             cmap = code_for(f, v)
-            ms, out = _run(sub, cmap, reps=reps)
+            ms, out = runner(sub, cmap, reps=reps)
             nbits = sum(cmap[ci].output_bits(n) for _, _, n, _ in sub)
             dis = 0.0 if f == 0 else _disagree(out, ref_out, nbits)
             rows.append({"f": f, "v": v, "ms": ms, "disagree": dis})
-            if dis <= max_disagree and (best is None or ms < best.ms):
-                best = Choice(f, v, ms, dis)
-        chosen[ci] = best
+        chosen[ci] = pick(rows, max_disagree)
+        if chosen[ci] is None:
+            raise ValueError(f"no candidate tiling of code {ci} is within max_disagree={max_disagree}")
         report[ci] = rows
-    code_objs = {ci: vit.Code(*codes[ci], f=chosen[ci].f, v=chosen[ci].v,
-                              mode=next(m for c, _, _, m in frames if c == ci)) for ci in chosen}
+    code_objs = {ci: make_code(*codes[ci], chosen[ci].f, chosen[ci].v,
+                               next(m for c, _, _, m in frames if c == ci)) for ci in chosen}
     wbest, wms = None, None
     for w in warps_options:
-        ms, _ = _run(frames, code_objs, warps=w, reps=reps)
+        ms, _ = runner(frames, code_objs, warps=w, reps=reps)
         report.setdefault("warps", []).append({"warps": w, "ms": ms})
         if wms is None or ms < wms:
             wbest, wms = w, ms

@@ -66,6 +66,8 @@ def load(path: str | None = None):
         "vit_metric_workspace": (sz, [vp, i32, i64, ctypes.c_float, i32]),
         "vit_metric_fwd": (i32, [vp, vp, i32, i64, ctypes.c_float, i32, vp, vp, sz, vp]),
         "vit_metric_bwd": (i32, [vp, vp, vp, i32, i64, ctypes.c_float, i32, vp, sz, vp, vp]),
+        "vit_probe_rate": (i32, [i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in list(sig.items()) + list(optional.items()):
         if not hasattr(L, name):
@@ -296,3 +298,16 @@ class ViterbiMetric(torch.autograd.Function):
 
 def path_metric(llr: torch.Tensor, code: Code, tau: float = 0.0, C: int = 64) -> torch.Tensor:
     return ViterbiMetric.apply(llr, code, tau, C)
+
+
+PROBE_KINDS = {"iadd": 0, "vmax16": 1, "imad": 2, "prmt": 3, "lop3": 4, "fadd": 5, "fmax": 6, "ex2": 7, "lg2": 8}
+
+
+def probe_rate(kind: str, ctas_per_sm: int = 4, warps: int = 8, iters: int = 2000, device=None):
+    """Instruction-rate microbenchmark (include/vit_probe.h): returns
+    (warp instructions of class ``kind`` per SM clock per SM, launch ms, SM count)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    rate, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(load().vit_probe_rate(PROBE_KINDS[kind], ctas_per_sm, warps, iters, _stream(dev), ctypes.byref(rate),
+                                 ctypes.byref(ms), ctypes.byref(sms)))
+    return rate.value, ms.value, sms.value

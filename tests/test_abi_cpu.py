@@ -34,15 +34,20 @@ def lib():
 
 
 def _declared():
-    with open(os.path.join(ROOT, "include", "vit.h")) as fh:
-        src = fh.read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(vit_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        with open(os.path.join(ROOT, "include", h)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(vit_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(lib):
     names = _declared()
-    assert "vit_decode" in names and "vit_metric_bwd" in names
+    assert "vit_decode" in names and "vit_metric_bwd" in names and "vit_probe_rate" in names
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, f"declared but not exported: {missing}"
 

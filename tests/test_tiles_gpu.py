@@ -1,0 +1,107 @@
+"""Parity of the 64-tiles-per-warp tile decoder with the CPU oracle for every
+compiled code.
+
+Single frames of at most 1024 tiles go to the warp-per-tile decoder, so the
+frames here are cut into more than 1024 tiles (f = 8 or 16): every case
+below runs the tile decoder (Alg. 1 + Alg. 2 on the overlapped tiles of Fig.
+relworks), including warp tasks whose last tiles are missing, a short last
+tile, windows clipped at both frame ends, asymmetric overlaps, saturated and
+all-zero LLRs, and an LLR buffer that starts at an odd address (byte loads
+instead of the 32-bit word loads).  Decoded bits are compared with
+``oracle.viterbi_blocked`` element by element.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2011_09337_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CODES = {
+    "k7": synth.CODE_K7_R12,
+    "k7swap": (7, 2, (0o133, 0o171)),
+    "k7r13": synth.CODE_K7_R13,
+    "k5": (5, 2, (0o23, 0o35)),
+    "k5b3": (5, 3, (0o25, 0o33, 0o37)),
+    "k3": (3, 2, (0o7, 0o5)),
+    "k4b4": (4, 4, (0o13, 0o15, 0o17, 0o11)),
+    "k6asym": (6, 2, (0o53, 0o46)),
+    "k9": synth.CODE_K9_R12,
+}
+
+
+@pytest.fixture(scope="module")
+def vit():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2011_09337_gb300 import vit as v
+    v.load()
+    return v
+
+
+def _enc(code):
+    K, beta, polys = code
+    return lambda x: oracle.encode(K, beta, polys, x)
+
+
+def _decode(vit, key, llr, n, f, v1, v2, mode, offset=0):
+    """Decodes through vit_decode_ws; ``offset`` places the LLRs that many
+    bytes into a larger device buffer."""
+    K, beta, polys = CODES[key]
+    c = vit.Code(K, beta, polys, f=f, v=v1, v1=v1, v2=v2, mode=mode)
+    flat = np.ascontiguousarray(llr).reshape(-1)
+    buf = torch.zeros(flat.size + 16, dtype=torch.int8, device="cuda")
+    buf[offset:offset + flat.size] = torch.from_numpy(flat).cuda()
+    x = buf[offset:offset + flat.size]
+    assert (x.data_ptr() % 4 == 0) == (offset % 4 == 0)
+    out = vit.decode(c, x, n=n)
+    torch.cuda.synchronize()
+    return synth.unpack_bits(out.cpu().numpy(), c.output_bits(n))
+
+
+# (n, f, v1, v2): more than 1024 tiles each, ragged last tiles and tasks
+CASES = [(9001, 8, 12, 12), (16 * 1100 + 5, 16, 40, 9), (8 * 1500, 8, 0, 30)]
+
+
+@pytest.mark.parametrize("key", list(CODES))
+@pytest.mark.parametrize("mode", [oracle.STREAM, oracle.TERMINATED, oracle.FREE_START])
+def test_tile_decoder_matches_oracle(vit, key, mode):
+    K, beta, polys = CODES[key]
+    tail = K - 1 if mode == oracle.TERMINATED else 0
+    for i, (n, f, v1, v2) in enumerate(CASES):
+        assert (n + f - 1) // f > 1024
+        s = synth.make_stream(_enc(CODES[key]), beta, n, 1.0 + i, seed=1000 * i + 10 * mode + K, tail=tail)
+        want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v1, v2, mode)[: n - tail]
+        got = _decode(vit, key, s.llr, n, f, v1, v2, mode)
+        np.testing.assert_array_equal(got, want, err_msg=f"{key} mode={mode} n={n} f={f} v1={v1} v2={v2}")
+
+
+@pytest.mark.parametrize("key", list(CODES))
+def test_tile_decoder_extreme_llrs(vit, key):
+    """Saturated +-127 LLRs (the widest metric spread the renormalisation
+    must hold), all-zero LLRs and +-1 LLRs (every comparison a tie)."""
+    K, beta, polys = CODES[key]
+    g = synth.rng(91 + K)
+    n, f, v = 8 * 1200 + 3, 8, 2 * (K - 1)
+    llrs = [np.where(g.random((n, beta)) < 0.5, -127, 127).astype(np.int8),
+            np.zeros((n, beta), np.int8),
+            g.integers(-1, 2, size=(n, beta)).astype(np.int8)]
+    for j, llr in enumerate(llrs):
+        want = oracle.viterbi_blocked(K, beta, polys, llr, f, v, v)
+        got = _decode(vit, key, llr, n, f, v, v, oracle.STREAM)
+        np.testing.assert_array_equal(got, want, err_msg=f"{key} llr set {j}")
+
+
+@pytest.mark.parametrize("key", ["k7", "k7r13", "k9", "k4b4"])
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_tile_decoder_unaligned_llrs(vit, key, offset):
+    """LLRs at an address that is not a multiple of 4: the warp tasks cannot
+    use 32-bit word loads and fall back to byte loads."""
+    K, beta, polys = CODES[key]
+    n, f, v = 16 * 1030 + 11, 16, 3 * (K - 1)
+    s = synth.make_stream(_enc(CODES[key]), beta, n, 2.5, seed=offset + 7 * K)
+    want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v)
+    got = _decode(vit, key, s.llr, n, f, v, v, oracle.STREAM, offset=offset)
+    np.testing.assert_array_equal(got, want)
