@@ -71,7 +71,11 @@ enum {
  * f = 0 decodes each frame as one tile (full-frame Viterbi, Alg. 1 + 2);
  * otherwise f must be a positive multiple of 8.  A window that does not start
  * at stage 0 starts with all path metrics equal.
- * Returns VIT_EUNSUPPORTED for a valid code with no compiled kernel.
+ * Every valid code is decoded.  Codes with a compiled kernel (among them
+ * (171,133), (133,171), (133,171,165) and (561,753)) run the fast tile
+ * decoders; any other generators run decoders that take the generators at
+ * run time (one warp per tile, the states over the lanes; slower), which have
+ * no parallel traceback.
  */
 int vit_create(vit_code** out, int K, int beta, const uint32_t* polys, int64_t f, int64_t v);
 
@@ -102,7 +106,7 @@ int vit_set_termination(vit_code* code, int mode);
  * the global index of that stage).  The decoded bits differ from the serial
  * traceback's.  f0: 0 (off, the default) or a positive multiple of 8.
  * Returns VIT_EUNSUPPORTED for codes without a compiled parallel-traceback
- * kernel (those whose 2^(K-1) states do not fit one lane: K > 7).
+ * kernel (K > 7, and codes decoded with generators taken at run time).
  */
 enum { VIT_PT_STORED = 0, VIT_PT_RANDOM = 1 };
 int vit_set_parallel_traceback(vit_code* code, int64_t f0, int rule, uint64_t seed);
@@ -250,7 +254,7 @@ int vit_metric_bwd(const vit_code* code, const float* llr, const float* grad_met
 /* ------------------------------------------------------------------ misc */
 
 const char* vit_last_error(void);
-/* 1 if a kernel is compiled for (K, beta, polys), else 0. */
+/* 1 if vit_create accepts (K, beta, polys), i.e. the code is valid, else 0. */
 int vit_code_supported(int K, int beta, const uint32_t* polys);
 
 #ifdef __cplusplus

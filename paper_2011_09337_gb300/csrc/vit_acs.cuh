@@ -100,44 +100,14 @@ VIT_HD uint32_t aout_rt(const uint32_t* polys, int beta, uint32_t R) {
   return o;
 }
 
-// Branch-pattern signs of a code whose generators are known only at run
-// time: s[x][br][b] = (-1)^{c_b} of the branch pattern c (Eq. 1, Eq. 2) of
-// branch br of butterfly x (br 0: 2x -> x, 1: 2x+1 -> x, 2: 2x -> x + S/2,
-// 3: 2x+1 -> x + S/2), 0 for b >= beta.  Passed to the decoder by value as a
-// kernel parameter, so every sign is a constant-bank operand of the
-// multiply-adds that form the candidates.
-struct GenTab {
-  int32_t s[32][4][4];
-};
-
-VIT_HD void make_gen_tab(int K, int beta, const uint32_t* polys, GenTab& t) {
-  const uint32_t S = 1u << (K - 1);
-  for (uint32_t x = 0; x < 32; x++)
-    for (int br = 0; br < 4; br++) {
-      const uint32_t R = 2u * x + (uint32_t)(br & 1) + ((br & 2) ? S : 0u);
-      const uint32_t c = (2u * x < S) ? aout_rt(polys, beta, R) : 0u;
-      for (int b = 0; b < 4; b++) t.s[x][br][b] = (b < beta && 2u * x < S) ? (((c >> b) & 1u) ? -1 : 1) : 0;
-    }
-}
-
 // A rate-1/beta code with constraint length K whose generators are known
-// only at run time.  The lane decoder (K <= 7) takes each butterfly's branch
-// patterns from a GenTab; the warp-per-tile decoders (any K) compute their
-// lanes' patterns from the generators.
+// only at run time.  It is decoded by the warp-per-tile decoders, whose
+// lanes form the branch patterns of their own states from the generators
+// once per tile.
 template <int K_, int B_>
 struct GCode {
   static constexpr int K = K_, BETA = B_, KM1 = K_ - 1, S = 1 << (K_ - 1);
-  static constexpr int NS = S, G = 1, NSB = ilog2c(NS);
-  static constexpr int WORDS = NS >= 16 ? NS / 16 : 1;
-  static constexpr int HALFP = NS >= 16 ? 8 : NS / 2;
-  static constexpr int ND = B_;  // a stage's branch metrics are its beta packed LLRs
-  static constexpr int U = 2;
-  static constexpr int DMAX = 127 * B_;
-  static constexpr int SPREAD = 4 * KM1 * 127 * B_ + 1;
-  static constexpr int RN_MAX = ((32767 - SPREAD) / DMAX - 1) / U;
-  static constexpr int RN = RN_MAX < 1 ? 1 : (RN_MAX > 32 ? 32 : RN_MAX);
-  static constexpr bool GENERIC = true, SYMMETRIC = false;
-  static_assert(SPREAD + 2 * DMAX < 32768, "decision differences must fit 16 bits");
+  static constexpr bool GENERIC = true;
   static_assert(K_ >= 3 && K_ <= 9, "K in [3, 9]");
   static_assert(B_ >= 2 && B_ <= 4, "beta in [2,4]");
 };
@@ -227,17 +197,12 @@ VIT_HD void stage_bm(const int (&lA)[C::BETA], const int (&lB)[C::BETA], StageBM
   int L[C::BETA];
 #pragma unroll
   for (int b = 0; b < C::BETA; b++) L[b] = lA[b] + lB[b] * 65536;
-  if constexpr (C::GENERIC) {
 #pragma unroll
-    for (int b = 0; b < C::BETA; b++) D.D[b] = (uint32_t)L[b];
-  } else {
+  for (int c = 0; c < C::ND; c++) {
+    int acc = 0;
 #pragma unroll
-    for (int c = 0; c < C::ND; c++) {
-      int acc = 0;
-#pragma unroll
-      for (int b = 0; b < C::BETA; b++) acc += ((c >> b) & 1) ? -L[b] : L[b];
-      D.D[c] = (uint32_t)acc;
-    }
+    for (int b = 0; b < C::BETA; b++) acc += ((c >> b) & 1) ? -L[b] : L[b];
+    D.D[c] = (uint32_t)acc;
   }
 }
 
@@ -267,35 +232,19 @@ VIT_HD int surv_pos(int s) {
 // (odd) of mi give successors x and x + S/2 in mo, with their decision words.
 template <class C>
 VIT_HD void butterfly(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const StageBM<C>& D, int x,
-                      uint32_t& E0, uint32_t& E1, const GenTab* gt) {
+                      uint32_t& E0, uint32_t& E1) {
   constexpr int H = C::NS / 2;
-  if constexpr (C::GENERIC) {
-    // candidate of branch br: predecessor metric + sum_b sign * packed LLR_b
-    uint32_t xc[4];
-#pragma unroll
-    for (int br = 0; br < 4; br++) {
-      uint32_t acc = mi[2 * x + (br & 1)];
-#pragma unroll
-      for (int b = 0; b < C::BETA; b++) acc += (uint32_t)gt->s[x][br][b] * D.D[b];
-      xc[br] = acc;
-    }
-    E0 = xc[0] - xc[1] + 0x8000u;
-    E1 = xc[2] - xc[3] + 0x8000u;
-    mo[x] = vmaxu2(xc[0], xc[1]);
-    mo[x + H] = vmaxu2(xc[2], xc[3]);
-  } else {
-    const uint32_t i0 = 2u * (uint32_t)x;
-    const uint32_t c00 = C::aout(i0), c01 = C::aout(i0 | 1u);
-    const uint32_t c10 = C::aout(i0 | (uint32_t)C::S), c11 = C::aout(i0 | (uint32_t)C::S | 1u);
-    const uint32_t x00 = add_bm<C>(mi[2 * x], D, c00), x01 = add_bm<C>(mi[2 * x + 1], D, c01);
-    const uint32_t x10 = add_bm<C>(mi[2 * x], D, c10), x11 = add_bm<C>(mi[2 * x + 1], D, c11);
-    E0 = x00 - x01 + 0x8000u;
-    // x10 - x11 = (x00 - x01) + (d(c10) - d(c11) - d(c00) + d(c01)): the
-    // bracket is the same for every butterfly with these patterns this stage
-    E1 = add_on_fma(E0, bmv<C>(D, c10) - bmv<C>(D, c11) - bmv<C>(D, c00) + bmv<C>(D, c01));
-    mo[x] = vmaxu2(x00, x01);
-    mo[x + H] = vmaxu2(x10, x11);
-  }
+  const uint32_t i0 = 2u * (uint32_t)x;
+  const uint32_t c00 = C::aout(i0), c01 = C::aout(i0 | 1u);
+  const uint32_t c10 = C::aout(i0 | (uint32_t)C::S), c11 = C::aout(i0 | (uint32_t)C::S | 1u);
+  const uint32_t x00 = add_bm<C>(mi[2 * x], D, c00), x01 = add_bm<C>(mi[2 * x + 1], D, c01);
+  const uint32_t x10 = add_bm<C>(mi[2 * x], D, c10), x11 = add_bm<C>(mi[2 * x + 1], D, c11);
+  E0 = x00 - x01 + 0x8000u;
+  // x10 - x11 = (x00 - x01) + (d(c10) - d(c11) - d(c00) + d(c01)): the
+  // bracket is the same for every butterfly with these patterns this stage
+  E1 = add_on_fma(E0, bmv<C>(D, c10) - bmv<C>(D, c11) - bmv<C>(D, c00) + bmv<C>(D, c01));
+  mo[x] = vmaxu2(x00, x01);
+  mo[x + H] = vmaxu2(x10, x11);
 }
 
 // Places the decisions of states s and s + HALFP (both tiles) into the
@@ -311,7 +260,7 @@ VIT_HD void gather2(uint32_t (&w)[C::WORDS], int s, uint32_t Es, uint32_t Ep) {
 // together, which keeps few decision words live.
 template <class C>
 VIT_HD void acs_stage(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const StageBM<C>& D,
-                      uint32_t (&w)[C::WORDS], const GenTab* gt = nullptr) {
+                      uint32_t (&w)[C::WORDS]) {
   constexpr int H = C::NS / 2;
   constexpr int HP = C::HALFP;
 #pragma unroll
@@ -321,7 +270,7 @@ VIT_HD void acs_stage(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const 
 #pragma unroll
     for (int x = 0; x < H; x++) {
       uint32_t E0, E1;
-      butterfly<C>(mi, mo, D, x, E0, E1, gt);
+      butterfly<C>(mi, mo, D, x, E0, E1);
       gather2<C>(w, x, E0, E1);
     }
   } else {
@@ -329,8 +278,8 @@ VIT_HD void acs_stage(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const 
     for (int x = 0; x < H; x++) {
       if (x & HP) continue;
       uint32_t Ea, Eb, Ec, Ed;  // successors x, x+H, x+HP, x+HP+H
-      butterfly<C>(mi, mo, D, x, Ea, Eb, gt);
-      butterfly<C>(mi, mo, D, x + HP, Ec, Ed, gt);
+      butterfly<C>(mi, mo, D, x, Ea, Eb);
+      butterfly<C>(mi, mo, D, x + HP, Ec, Ed);
       gather2<C>(w, x, Ea, Ec);
       gather2<C>(w, x + H, Eb, Ed);
     }
@@ -512,17 +461,12 @@ VIT_HD void pairs_from_words(const uint32_t (&w)[2][C::U * C::BETA / 4], int (&L
 
 template <class C>
 VIT_HD void bm_from_pairs(const int (&L)[C::BETA], StageBM<C>& D) {
-  if constexpr (C::GENERIC) {
 #pragma unroll
-    for (int b = 0; b < C::BETA; b++) D.D[b] = (uint32_t)L[b];
-  } else {
+  for (int c = 0; c < C::ND; c++) {
+    int acc = 0;
 #pragma unroll
-    for (int c = 0; c < C::ND; c++) {
-      int acc = 0;
-#pragma unroll
-      for (int b = 0; b < C::BETA; b++) acc += ((c >> b) & 1) ? -L[b] : L[b];
-      D.D[c] = (uint32_t)acc;
-    }
+    for (int b = 0; b < C::BETA; b++) acc += ((c >> b) & 1) ? -L[b] : L[b];
+    D.D[c] = (uint32_t)acc;
   }
 }
 
@@ -562,7 +506,7 @@ VIT_HD void load_words(const Slab& sl, int i, uint32_t (&w)[C::WORDS]) {
 // the known-start reset, add-compare-select from mi to mo, survivor store.
 template <class C>
 VIT_HD void fwd_stage(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const Half (&hw)[2], int i, bool masked,
-                      uint32_t M, const int (&lv)[2][C::BETA], Slab sl, const GenTab* gt = nullptr) {
+                      uint32_t M, const int (&lv)[2][C::BETA], Slab sl) {
   int lA[C::BETA], lB[C::BETA];
 #pragma unroll
   for (int b = 0; b < C::BETA; b++) {
@@ -583,20 +527,20 @@ VIT_HD void fwd_stage(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const Half (
   StageBM<C> D;
   stage_bm<C>(lA, lB, D);
   uint32_t w[C::WORDS];
-  acs_stage<C>(mi, mo, D, w, gt);
+  acs_stage<C>(mi, mo, D, w);
   store_words(sl.base + (int64_t)i * sl.stride, w, C::WORDS);
 }
 
 // Forward stage fed by word loads (every window of the warp has started).
 template <class C, int u>
 VIT_HD void fwd_stage_words(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], int i,
-                            const uint32_t (&w)[2][C::U * C::BETA / 4], Slab sl, const GenTab* gt = nullptr) {
+                            const uint32_t (&w)[2][C::U * C::BETA / 4], Slab sl) {
   int L[C::BETA];
   pairs_from_words<C, u>(w, L);
   StageBM<C> D;
   bm_from_pairs<C>(L, D);
   uint32_t wd[C::WORDS];
-  acs_stage<C>(mi, mo, D, wd, gt);
+  acs_stage<C>(mi, mo, D, wd);
   store_words(sl.base + (int64_t)i * sl.stride, wd, C::WORDS);
 }
 
@@ -748,8 +692,7 @@ VIT_HD void traceback_pair(const Half (&hw)[2], int Lw, const int (&s0)[2], Slab
 // least every active window length); masked_until: first iteration from which
 // every window of the warp has started.
 template <class C>
-VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t M, Slab sl, bool words_ok,
-                        const GenTab* gt = nullptr) {
+VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t M, Slab sl, bool words_ok) {
   static_assert(C::G == 1 && C::S <= 64, "all states of a tile pair in one lane");
   uint32_t ma[C::NS], mb[C::NS];
 #pragma unroll
@@ -770,8 +713,8 @@ VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t 
         const int i0 = g * C::U;
         LlrGroup<C> lg;
         load_group<C>(hw, i0, lg);
-        fwd_stage<C>(ma, mb, hw, i0, true, M, lg.v[0], sl, gt);
-        fwd_stage<C>(mb, ma, hw, i0 + 1, true, M, lg.v[1], sl, gt);
+        fwd_stage<C>(ma, mb, hw, i0, true, M, lg.v[0], sl);
+        fwd_stage<C>(mb, ma, hw, i0 + 1, true, M, lg.v[1], sl);
         if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
       }
       constexpr int NW = C::U * C::BETA / 4;
@@ -780,8 +723,8 @@ VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t 
       for (; g < ngroups; g++) {
         const int i0 = g * C::U;
         if (g + 1 < ngroups) load_group_words<C>(hw, i0 + C::U, wn);  // prefetch the next group
-        fwd_stage_words<C, 0>(ma, mb, i0, wc, sl, gt);
-        fwd_stage_words<C, 1>(mb, ma, i0 + 1, wc, sl, gt);
+        fwd_stage_words<C, 0>(ma, mb, i0, wc, sl);
+        fwd_stage_words<C, 1>(mb, ma, i0 + 1, wc, sl);
         if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
 #pragma unroll
         for (int h = 0; h < 2; h++)
@@ -801,8 +744,8 @@ VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t 
           load_group_fast<C>(hw, i0 + C::U, nxt);
       }
       const bool masked = i0 < masked_until;
-      fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl, gt);
-      fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl, gt);
+      fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl);
+      fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl);
       if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
       cur = nxt;
     }

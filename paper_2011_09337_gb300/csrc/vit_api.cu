@@ -214,6 +214,42 @@ const MixEntry* find_mixed(const CodeEntry* x, const CodeEntry* y, bool* swapped
   return nullptr;
 }
 
+struct GenReg {
+  int K, beta;
+  const CodeEntry* entry;
+  LaunchFn warp;
+};
+std::vector<GenReg>& gen_registry() {
+  static std::vector<GenReg> r;
+  return r;
+}
+GenReg* gen_slot(int K, int beta) {
+  for (GenReg& r : gen_registry())
+    if (r.K == K && r.beta == beta) return &r;
+  gen_registry().push_back(GenReg{K, beta, nullptr, nullptr});
+  return &gen_registry().back();
+}
+void register_generic(const CodeEntry* e) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  gen_slot(e->K, e->beta)->entry = e;
+}
+void register_warp_generic(int K, int beta, LaunchFn launch) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  gen_slot(K, beta)->warp = launch;
+}
+const CodeEntry* find_generic(int K, int beta) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (const GenReg& r : gen_registry())
+    if (r.K == K && r.beta == beta) return r.entry;
+  return nullptr;
+}
+LaunchFn find_warp_generic(int K, int beta) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (const GenReg& r : gen_registry())
+    if (r.K == K && r.beta == beta) return r.warp;
+  return nullptr;
+}
+
 const CodeEntry* find_code(int K, int beta, const uint32_t* polys) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   for (const CodeEntry& e : registry()) {
@@ -232,7 +268,7 @@ const char* vit_last_error(void) { return g_err.c_str(); }
 
 int vit_code_supported(int K, int beta, const uint32_t* polys) {
   if (!code_args_ok(K, beta, polys)) return 0;
-  return find_code(K, beta, polys) != nullptr;
+  return find_code(K, beta, polys) != nullptr || find_generic(K, beta) != nullptr;
 }
 
 int vit_create(vit_code** out, int K, int beta, const uint32_t* polys, int64_t f, int64_t v) {
@@ -243,8 +279,11 @@ int vit_create(vit_code** out, int K, int beta, const uint32_t* polys, int64_t f
   if (f < 0 || v < 0 || (f % 8) != 0 || f > ((int64_t)1 << 30) || v > ((int64_t)1 << 20))
     return fail(VIT_EINVAL, "invalid tiling f=%lld v=%lld (f: 0 or a positive multiple of 8)", (long long)f,
                 (long long)v);
+  // a kernel compiled for these generators, else the decoders that take
+  // the generators at run time
   const CodeEntry* e = find_code(K, beta, polys);
-  if (e == nullptr) return fail(VIT_EUNSUPPORTED, "no kernel compiled for K=%d beta=%d with these generators", K, beta);
+  if (e == nullptr) e = find_generic(K, beta);
+  if (e == nullptr) return fail(VIT_EUNSUPPORTED, "no kernel compiled for K=%d beta=%d", K, beta);
   vit_code* c = new (std::nothrow) vit_code;
   if (c == nullptr) return fail(VIT_ENOMEM, "out of host memory");
   memset(c, 0, sizeof *c);
@@ -255,7 +294,7 @@ int vit_create(vit_code** out, int K, int beta, const uint32_t* polys, int64_t f
   c->v1 = c->v2 = v;
   c->mode = VIT_STREAM;
   c->entry = e;
-  c->warp_launch = find_warp(e);
+  c->warp_launch = e->generic ? find_warp_generic(K, beta) : find_warp(e);
   *out = c;
   return VIT_OK;
 }
@@ -303,7 +342,7 @@ int vit_set_parallel_traceback(vit_code* c, int64_t f0, int rule, uint64_t seed)
     c->pt_launch = nullptr;
     return VIT_OK;
   }
-  const LaunchFn l = find_pt(c->entry);
+  const LaunchFn l = c->entry->generic ? nullptr : find_pt(c->entry);
   if (l == nullptr)
     return fail(VIT_EUNSUPPORTED, "no parallel-traceback kernel compiled for K=%d beta=%d with these generators",
                 c->K, c->beta);
@@ -338,7 +377,7 @@ static size_t slab_task_words(const vit_code* c, int64_t n) {
   const int64_t L = max_window(c, n);
   const int64_t U = c->entry->unroll;
   const int64_t Lr = (L + U - 1) / U * U;
-  return (size_t)Lr * 32 * c->entry->words;
+  return (size_t)Lr * c->entry->slab_lanes * c->entry->words;
 }
 
 size_t vit_decode_workspace(const vit_code* c, int64_t n) {
@@ -400,6 +439,7 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
   a.slab = slab;
   a.task_words = (int64_t)tw;
   a.task_base = 0;
+  for (int b = 0; b < c->beta; b++) a.polys[b] = c->polys[b];
   if (c->pt_f0 > 0) {
     a.pt_f0 = c->pt_f0;
     a.pt_rule = c->pt_rule;
@@ -499,6 +539,7 @@ struct vit_batch {
     uint8_t* d_pt = nullptr;
     Tiling tl;
     uint32_t M;
+    uint32_t polys[4] = {0, 0, 0, 0};
     int nframes;
     int64_t ntiles, ntasks, task_words;
     Frame* d_frames = nullptr;
@@ -612,6 +653,7 @@ KArgs group_args(const vit_batch::Group& g) {
   a.pt_seed = g.pt_seed;
   a.pt_nsub = g.pt_nsub;
   a.pt_states = g.d_pt;
+  for (int b = 0; b < 4; b++) a.polys[b] = g.polys[b];
   return a;
 }
 
@@ -819,7 +861,8 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     for (size_t k = 0; k < leaders.size(); k++) {
       const vit_code* l = leaders[k];
       if (l->entry == c->entry && l->f == c->f && l->v1 == c->v1 && l->v2 == c->v2 && l->pt_f0 == c->pt_f0 &&
-          (c->pt_f0 == 0 || (l->pt_rule == c->pt_rule && l->pt_seed == c->pt_seed)))
+          (c->pt_f0 == 0 || (l->pt_rule == c->pt_rule && l->pt_seed == c->pt_seed)) &&
+          (!c->entry->generic || memcmp(l->polys, c->polys, sizeof c->polys) == 0))
         gi = (int)k;
     }
     if (gi < 0) {
@@ -843,6 +886,7 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
     vit_batch::Group g;
     g.entry = c->entry;
     g.launch = c->pt_f0 > 0 ? c->pt_launch : c->entry->launch;  // replaced below for short frames
+    for (int q = 0; q < c->beta; q++) g.polys[q] = c->polys[q];
     g.pt_f0 = c->pt_f0;
     g.pt_rule = c->pt_rule;
     g.pt_seed = c->pt_seed;
@@ -913,7 +957,7 @@ int vit_batch_plan(vit_batch** out, const vit_frame* frames, int nframes, int fl
       L = tile_len_host[(size_t)t] > L ? tile_len_host[(size_t)t] : L;
     }
     const int64_t U = c->entry->unroll;
-    g.task_words = ((maxw + U - 1) / U * U) * 32 * c->entry->words;
+    g.task_words = ((maxw + U - 1) / U * U) * c->entry->slab_lanes * c->entry->words;
     g.d_frames = (Frame*)dalloc(sizeof(Frame) * g.nframes);
     g.d_tile0 = (int64_t*)dalloc(sizeof(int64_t) * g.nframes);
     g.d_slab = (uint32_t*)dalloc((size_t)g.ntasks * g.task_words * 4);

@@ -40,11 +40,8 @@ struct KArgs {
   uint64_t pt_seed;
   uint8_t* pt_states;
   int64_t pt_nsub;
-  // codes known only at run time: the generators (read by the warp-per-tile
-  // decoders) and, on the host, the branch-sign table that the launcher of the
-  // lane decoder passes as a kernel parameter
+  // the generators (read by the decoders of codes known only at run time)
   uint32_t polys[4];
-  const GenTab* gen;
 };
 
 VIT_HD int64_t find_frame(const int64_t* tile0, int nframes, int64_t gt) {
@@ -104,9 +101,9 @@ __device__ __forceinline__ void task_setup(const KArgs& a, int64_t task, int lan
   sl = Slab{a.slab + task * a.task_words + lane * C::WORDS, 32 * C::WORDS};
 }
 
-// Decodes warp task `task` of one code (gt: branch signs of a GCode).
+// Decodes warp task `task` of one code.
 template <class C, bool kWords = true>
-__device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane, const GenTab* tab = nullptr) {
+__device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane) {
   Half hw[2];
   int64_t gt[2], e1f[2];
   int Lw, mu;
@@ -121,7 +118,7 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane,
                              (uintptr_t)((hw[h].t0 - hw[h].start) * C::BETA)) % 4u == 0u);
   const bool words_ok = kWords && __all_sync(0xffffffffu, aligned);
   if constexpr (C::G == 1)
-    decode_pair<C>(hw, Lw, mu, a.M, sl, words_ok, tab);
+    decode_pair<C>(hw, Lw, mu, a.M, sl, words_ok);
   else
     decode_pair_rot<C, kWords>(hw, Lw, mu, a.M, sl, lane, words_ok);
 }
@@ -136,16 +133,6 @@ __global__ void __maxnreg__((C::G > 1 && kWords) ? kMaxRegsRotWords : kMaxRegs) 
   const int64_t task = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (task >= a.ntasks) return;  // warp-uniform
   run_task<C, kWords>(a, task, lane);
-}
-
-// The lane decoder of a code known only at run time: the branch signs arrive
-// by value (constant-bank operands of the candidate multiply-adds).
-template <class C>
-__global__ void __maxnreg__(kMaxRegs) decode_tiles_gen_kernel(const KArgs a, const __grid_constant__ GenTab tab) {
-  const int lane = threadIdx.x & 31;
-  const int64_t task = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (task >= a.ntasks) return;  // warp-uniform
-  run_task<C, true>(a, task, lane, &tab);
 }
 
 // Persistent kernel over the tasks of two codes: each warp takes the next
@@ -225,33 +212,11 @@ cudaError_t launch_tasks(const KArgs& a, int warps, cudaStream_t s) {
   return cudaSuccess;
 }
 
-// The same for kernels that also take the code's branch-sign table.
-template <void (*kernel)(const KArgs, const GenTab)>
-cudaError_t launch_tasks_gen(const KArgs& a, int warps, cudaStream_t s) {
-  if (a.gen == nullptr) return cudaErrorInvalidValue;
-  if (warps < 1 || warps > 8) warps = kWarpsPerCta;
-  const int64_t maxc = (int64_t)1 << 30;
-  for (int64_t t0 = a.task_base; t0 < a.ntasks; t0 += maxc * warps) {
-    KArgs b = a;
-    b.task_base = t0;
-    const int64_t tasks = (a.ntasks - t0 < maxc * warps) ? a.ntasks - t0 : maxc * warps;
-    const unsigned grid = (unsigned)((tasks + warps - 1) / warps);
-    kernel<<<grid, warps * 32, 0, s>>>(b, *a.gen);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
 template <class C>
 cudaError_t launch_decode(const KArgs& a, int warps, cudaStream_t s) {
   return launch_tasks<decode_tiles_kernel<C, true>>(a, warps, s);
 }
 
-template <class C>
-cudaError_t launch_decode_gen(const KArgs& a, int warps, cudaStream_t s) {
-  return launch_tasks_gen<decode_tiles_gen_kernel<C>>(a, warps, s);
-}
 
 template <class C>
 cudaError_t launch_decode_bytes(const KArgs& a, int warps, cudaStream_t s) {
@@ -289,12 +254,6 @@ constexpr CodeEntry make_entry() {
                    64 / C::G, 32, 0, &launch_decode<C>, bytes_launcher<C>()};
 }
 
-// The lane decoder of every code of (K, beta) with K <= 7 (GCode).
-template <class C>
-constexpr CodeEntry make_gen_entry() {
-  return CodeEntry{C::K, C::BETA, {0, 0, 0, 0}, C::WORDS, C::U, 64, 32, 1, &launch_decode_gen<C>,
-                   &launch_decode_gen<C>};
-}
 #endif
 
 // Registry filled by the per-code translation units.
@@ -315,15 +274,12 @@ LaunchFn find_pt(const CodeEntry* e);
 void register_warp(const MixKey& k, LaunchFn launch);
 LaunchFn find_warp(const CodeEntry* e);
 // Decoders for codes known only at run time, by (K, beta): the tile decoder
-// entry (the lane decoder for K <= 7, one warp per tile for K = 8, 9), the
-// single-frame warp-per-tile decoder (K <= 7) and the parallel traceback
-// (K <= 7).
+// entry (one warp per tile, decisions in the slab, any window) and the
+// single-frame warp-per-tile decoder with decisions in shared memory (K <= 7).
 void register_generic(const CodeEntry* e);
 const CodeEntry* find_generic(int K, int beta);
 void register_warp_generic(int K, int beta, LaunchFn launch);
 LaunchFn find_warp_generic(int K, int beta);
-void register_pt_generic(int K, int beta, LaunchFn launch);
-LaunchFn find_pt_generic(int K, int beta);
 
 }  // namespace vit
 
@@ -341,7 +297,6 @@ struct vit_code {
   uint64_t pt_seed;
   vit::LaunchFn pt_launch;
   vit::LaunchFn warp_launch;  // warp-per-tile decoder, or nullptr
-  vit::GenTab* gen;           // branch signs of a code served by a generic entry, else nullptr
 };
 
 namespace vit {

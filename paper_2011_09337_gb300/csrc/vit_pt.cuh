@@ -153,8 +153,7 @@ VIT_HD void pt_traceback_pair(const Half (&hw)[2], const int64_t (&e1f)[2], cons
 // before every window has started still use masked byte loads).
 template <class C>
 VIT_HD void decode_pair_pt(const Half (&hw)[2], const int64_t (&e1f)[2], int Lw, int masked_until, uint32_t M,
-                           Slab sl, int64_t v2, const PtParams& pt, uint8_t* const (&st)[2], bool words_ok,
-                           const GenTab* gt = nullptr) {
+                           Slab sl, int64_t v2, const PtParams& pt, uint8_t* const (&st)[2], bool words_ok) {
   static_assert(C::G == 1 && C::U == 2, "one lane per tile pair");
   uint32_t ma[C::NS], mb[C::NS];
 #pragma unroll
@@ -183,9 +182,9 @@ VIT_HD void decode_pair_pt(const Half (&hw)[2], const int64_t (&e1f)[2], int Lw,
         const int i0 = g * C::U;
         LlrGroup<C> lg;
         load_group<C>(hw, i0, lg);
-        fwd_stage<C>(ma, mb, hw, i0, true, M, lg.v[0], sl, gt);
+        fwd_stage<C>(ma, mb, hw, i0, true, M, lg.v[0], sl);
         capture(mb, i0);
-        fwd_stage<C>(mb, ma, hw, i0 + 1, true, M, lg.v[1], sl, gt);
+        fwd_stage<C>(mb, ma, hw, i0 + 1, true, M, lg.v[1], sl);
         capture(ma, i0 + 1);
         if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
       }
@@ -195,9 +194,9 @@ VIT_HD void decode_pair_pt(const Half (&hw)[2], const int64_t (&e1f)[2], int Lw,
       for (; g < ngroups; g++) {
         const int i0 = g * C::U;
         if (g + 1 < ngroups) load_group_words<C>(hw, i0 + C::U, wn);  // prefetch the next group
-        fwd_stage_words<C, 0>(ma, mb, i0, wc, sl, gt);
+        fwd_stage_words<C, 0>(ma, mb, i0, wc, sl);
         capture(mb, i0);
-        fwd_stage_words<C, 1>(mb, ma, i0 + 1, wc, sl, gt);
+        fwd_stage_words<C, 1>(mb, ma, i0 + 1, wc, sl);
         capture(ma, i0 + 1);
         if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
 #pragma unroll
@@ -218,9 +217,9 @@ VIT_HD void decode_pair_pt(const Half (&hw)[2], const int64_t (&e1f)[2], int Lw,
           load_group_fast<C>(hw, i0 + C::U, nxt);
       }
       const bool masked = i0 < masked_until;
-      fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl, gt);
+      fwd_stage<C>(ma, mb, hw, i0, masked, M, cur.v[0], sl);
       capture(mb, i0);
-      fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl, gt);
+      fwd_stage<C>(mb, ma, hw, i0 + 1, masked, M, cur.v[1], sl);
       capture(ma, i0 + 1);
       if ((g % C::RN) == C::RN - 1) renorm<C>(ma);
       cur = nxt;

@@ -95,7 +95,7 @@ __device__ __forceinline__ void warp_stage(int (&m)[C::S > 32 ? 2 : 1], uint32_t
 // bytes by shuffle, off the metrics' dependency chain; lane l keeps the
 // ballots of stage i0 + l and the warp stores a block's words together.
 template <class C>
-__device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int lane) {
+__device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int lane, const uint32_t* polys) {
   static_assert(C::S <= 64 && C::BETA <= 4, "states of one tile over the 32 lanes; LLR bytes in one word");
   constexpr int S = C::S;
   constexpr int R = S > 32 ? 2 : 1;  // states per lane: R * lane + r
@@ -106,8 +106,13 @@ __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int l
   for (int r = 0; r < R; r++) {
     const int j = R * lane + r;
     m[r] = (h.known && j != 0) ? -(int)M : 0;
-    cA[r] = C::aout(2u * (uint32_t)j);
-    cB[r] = C::aout(2u * (uint32_t)j + 1u);
+    if constexpr (C::GENERIC) {
+      cA[r] = aout_rt(polys, C::BETA, 2u * (uint32_t)j);
+      cB[r] = aout_rt(polys, C::BETA, 2u * (uint32_t)j + 1u);
+    } else {
+      cA[r] = C::aout(2u * (uint32_t)j);
+      cB[r] = C::aout(2u * (uint32_t)j + 1u);
+    }
   }
   const bool live = R * lane < S;
   const int8_t* llr = h.llr + h.t0 * C::BETA;
@@ -186,6 +191,159 @@ __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int l
       if (i - k >= ib) J = 2u * J + (uint32_t)((w[k] >> (J & (uint32_t)(S - 1))) & 1ull);
     const int lo = (i - 7 > ib ? i - 7 : ib);  // lowest iteration read so far
     tb_emit(J, lo - C::KM1, r0, r1, nb, out);
+  }
+}
+
+// One warp per tile for codes known only at run time (any K in [3, 9]), with
+// the tile's decisions in global memory, so any window length and any number
+// of tiles.  Lane l holds the 32-bit metrics of states R l + r (R = S / 32
+// for S >= 32; R = 1, lanes l < S, for smaller trellises).  The predecessors
+// 2s, 2s + 1 (mod S) of state R l + r are registers 2r, 2r + 1 (mod R) of
+// lane 2l (r < R/2) or 2l + 1 (mod 32), so a stage takes all R registers of
+// those two lanes by shuffle.  The branch patterns of a lane's states (Eq. 1)
+// are formed once from the generators.  Decisions (Eq. 4): ballot r of a
+// stage has bit l = decision of state R l + r; lane k keeps the R ballots of
+// stage i0 + k of each block of 32 stages and the warp stores the block's
+// words together (R words per stage).  Metrics are renormalised by state 0's
+// metric every 1024 stages, so their differences, which decide every
+// comparison, are those of unbounded integers for any window length.
+// Traceback (Alg. 2): every lane follows the same state; per block of 32
+// stages lane k loads stage k's R words, and each step selects the word of
+// the current state's register and takes it from the stage's lane by
+// shuffle.
+template <class C>
+__device__ void decode_tile_warp_gen(const Half& h, uint32_t M, uint32_t* dec, int lane, const uint32_t* polys) {
+  constexpr int S = C::S;
+  constexpr int R = S >= 32 ? S / 32 : 1;
+  const int L = (int)(h.t1 - h.t0);
+  const bool live = R * lane < S;
+  int m[R];
+  uint32_t cA[R], cB[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int j = R * lane + r;
+    m[r] = (h.known && j != 0) ? -(int)M : 0;
+    cA[r] = aout_rt(polys, C::BETA, 2u * (uint32_t)j);
+    cB[r] = aout_rt(polys, C::BETA, 2u * (uint32_t)j + 1u);
+  }
+  const int8_t* llr = h.llr + h.t0 * C::BETA;
+  const int la = (2 * lane) & (R == 1 ? S - 1 : 31), lb = (2 * lane + 1) & (R == 1 ? S - 1 : 31);
+  uint32_t nxt = warp_llr_word<C>(llr, lane, L);
+  for (int i0 = 0; i0 < L; i0 += 32) {
+    const uint32_t cur = nxt;
+    nxt = warp_llr_word<C>(llr, i0 + 32 + lane, L);
+    const int cnt = (L - i0 < 32) ? L - i0 : 32;
+    uint32_t keep[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) keep[r] = 0u;
+    for (int k = 0; k < cnt; k++) {
+      const uint32_t pk = __shfl_sync(0xffffffffu, cur, k);
+      int l[C::BETA];
+#pragma unroll
+      for (int b = 0; b < C::BETA; b++) l[b] = (int)(int8_t)(uint8_t)(pk >> (8 * b));
+      int qa[R], qb[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        qa[r] = __shfl_sync(0xffffffffu, m[r], la);
+        qb[r] = __shfl_sync(0xffffffffu, m[r], lb);
+      }
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        int p0, p1;
+        if constexpr (R == 1) {
+          p0 = qa[0];
+          p1 = qb[0];
+        } else {
+          p0 = (2 * r < R) ? qa[2 * r] : qb[2 * r - R];
+          p1 = (2 * r < R) ? qa[2 * r + 1] : qb[2 * r - R + 1];
+        }
+        const int x0 = p0 + warp_delta<C>(l, cA[r]), x1 = p1 + warp_delta<C>(l, cB[r]);
+        const uint32_t bal = __ballot_sync(0xffffffffu, live && x1 > x0);  // ties keep the even predecessor
+        keep[r] = (lane == k) ? bal : keep[r];
+        m[r] = x1 > x0 ? x1 : x0;
+      }
+    }
+    if (i0 + lane < L) {
+      uint32_t* p = dec + (int64_t)(i0 + lane) * R;
+      if constexpr (R == 1) {
+        p[0] = keep[0];
+      } else if constexpr (R == 2) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(keep[0], keep[1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < R / 4; q++)
+          reinterpret_cast<uint4*>(p)[q] = make_uint4(keep[4 * q], keep[4 * q + 1], keep[4 * q + 2], keep[4 * q + 3]);
+      }
+    }
+    if (((i0 >> 5) & 31) == 31) {  // every 1024 stages: subtract state 0's metric
+      const int ref = __shfl_sync(0xffffffffu, m[0], 0);
+#pragma unroll
+      for (int r = 0; r < R; r++) m[r] -= ref;
+    }
+  }
+  // traceback start: argmax, ties to the lowest state
+  int best = R * lane, bv = m[0];
+#pragma unroll
+  for (int r = 1; r < R; r++)
+    if (m[r] > bv) {
+      bv = m[r];
+      best = R * lane + r;
+    }
+  if (!live) {
+    best = S;
+    bv = -2147483647 - 1;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int ov = __shfl_xor_sync(0xffffffffu, bv, o), ob = __shfl_xor_sync(0xffffffffu, best, o);
+    if (ov > bv || (ov == bv && ob < best)) {
+      bv = ov;
+      best = ob;
+    }
+  }
+  if (h.e1 <= h.e0) return;
+  // as in the other tracebacks: the decision read at iteration i is the
+  // decoded bit of iteration i - (K-1); J = 2J + d kept unmasked holds the
+  // decoded bits from its low end; bytes are taken at checkpoints every 8
+  const int r0 = (int)(h.e0 - h.t0), r1 = (int)(h.e1 - h.t0);
+  int nb = (r1 - r0 + 7) / 8 - 1;
+  uint8_t* const out = h.out + (h.e0 >> 3);
+  uint32_t J = h.end_zero ? 0u : (uint32_t)best;
+  if (lane == 0) tb_emit(J, L - C::KM1, r0, r1, nb, out);  // bytes made of start-state bits only
+  const int ib = r0 + C::KM1;                              // lowest iteration read
+  if (ib >= L) return;
+  // blocks of 32 stages [b0, b0 + 32) aligned to ib, the highest cut at L
+  for (int b0 = ib + 32 * ((L - 1 - ib) / 32); b0 >= ib; b0 -= 32) {
+    uint32_t w[R];
+    const int my = b0 + lane;
+    if (my < L) {
+      const uint32_t* p = dec + (int64_t)my * R;
+      if constexpr (R == 1) {
+        w[0] = p[0];
+      } else if constexpr (R == 2) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        w[0] = v.x, w[1] = v.y;
+      } else {
+#pragma unroll
+        for (int q = 0; q < R / 4; q++) {
+          const uint4 v = reinterpret_cast<const uint4*>(p)[q];
+          w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; r++) w[r] = 0u;
+    }
+    const int top = (L - b0 < 32) ? L - b0 : 32;
+    for (int k = top - 1; k >= 0; k--) {
+      const uint32_t st = J & (uint32_t)(S - 1);
+      uint32_t sel = w[0];
+#pragma unroll
+      for (int r = 1; r < R; r++) sel = ((st & (uint32_t)(R - 1)) == (uint32_t)r) ? w[r] : sel;
+      const uint32_t word = __shfl_sync(0xffffffffu, sel, k);
+      J = 2u * J + ((word >> (st / R)) & 1u);
+      if (((b0 + k - ib) & 7) == 0 && lane == 0) tb_emit(J, b0 + k - C::KM1, r0, r1, nb, out);
+    }
   }
 }
 #endif

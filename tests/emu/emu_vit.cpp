@@ -14,8 +14,7 @@
 using namespace vit;
 
 template <class C>
-static int emu(const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v2, int mode, int M, uint8_t* out,
-               const GenTab* gt = nullptr) {
+static int emu(const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v2, int mode, int M, uint8_t* out) {
   Frame fr{llr, out, n, mode == 1 ? n - (C::K - 1) : n, mode};
   Tiling tl{f, v1, v2};
   const int64_t ntiles = tile_count(n, f);
@@ -47,7 +46,7 @@ static int emu(const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v2, 
     for (int l = 0; l < 32; l++) {
       if (!hw[l][0].active && !hw[l][1].active) continue;
       Slab sl{slab.data(), C::WORDS};
-      decode_pair<C>(hw[l], Lw, masked_until, (uint32_t)M, sl, words, gt);
+      decode_pair<C>(hw[l], Lw, masked_until, (uint32_t)M, sl, words);
     }
   }
   return 0;
@@ -56,7 +55,7 @@ static int emu(const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v2, 
 // The same with the parallel traceback (subframes of f0, start rule, seed).
 template <class C>
 static int emu_pt(const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v2, int mode, int M, int64_t f0,
-                  int rule, uint64_t seed, uint8_t* out, const GenTab* gt = nullptr) {
+                  int rule, uint64_t seed, uint8_t* out) {
   Frame fr{llr, out, n, mode == 1 ? n - (C::K - 1) : n, mode};
   Tiling tl{f, v1, v2};
   const PtParams pt{f0, rule, seed};
@@ -96,7 +95,7 @@ static int emu_pt(const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v
       Slab sl{slab.data(), C::WORDS};
       uint8_t* const st[2] = {states.data() + (task * 64 + 2 * l) * nsub,
                               states.data() + (task * 64 + 2 * l + 1) * nsub};
-      decode_pair_pt<C>(hw[l], e1f[l], Lw, masked_until, (uint32_t)M, sl, v2, pt, st, words, gt);
+      decode_pair_pt<C>(hw[l], e1f[l], Lw, masked_until, (uint32_t)M, sl, v2, pt, st, words);
     }
   }
   return 0;
@@ -123,38 +122,3 @@ EMU(emu_k5_23_35, 5, 2, 023, 035)
 EMU(emu_k3_7_5, 3, 2, 07, 05)
 EMU(emu_k4_b4, 4, 4, 013, 015, 017, 011)
 EMU(emu_k6_asym, 6, 2, 053, 046)
-
-// Codes known only at run time (GCode, K <= 7): the generators arrive as an
-// argument and the butterflies take their branch signs from a GenTab built
-// from them, as the library does for codes without a compiled kernel.
-template <int K, int B>
-static int emu_gen_kb(const uint32_t* polys, const int8_t* llr, int64_t n, int64_t f, int64_t v1, int64_t v2,
-                      int mode, int M, int64_t f0, int rule, uint64_t seed, uint8_t* out) {
-  GenTab tab;
-  make_gen_tab(K, B, polys, tab);
-  if (f0 > 0) return emu_pt<GCode<K, B>>(llr, n, f, v1, v2, mode, M, f0, rule, seed, out, &tab);
-  return emu<GCode<K, B>>(llr, n, f, v1, v2, mode, M, out, &tab);
-}
-
-template <int K>
-static int emu_gen_k(int beta, const uint32_t* polys, const int8_t* llr, int64_t n, int64_t f, int64_t v1,
-                     int64_t v2, int mode, int M, int64_t f0, int rule, uint64_t seed, uint8_t* out) {
-  switch (beta) {
-    case 2: return emu_gen_kb<K, 2>(polys, llr, n, f, v1, v2, mode, M, f0, rule, seed, out);
-    case 3: return emu_gen_kb<K, 3>(polys, llr, n, f, v1, v2, mode, M, f0, rule, seed, out);
-    case 4: return emu_gen_kb<K, 4>(polys, llr, n, f, v1, v2, mode, M, f0, rule, seed, out);
-  }
-  return -1;
-}
-
-extern "C" int emu_gen(int K, int beta, const uint32_t* polys, const int8_t* llr, int64_t n, int64_t f, int64_t v1,
-                       int64_t v2, int mode, int M, int64_t f0, int rule, uint64_t seed, uint8_t* out) {
-  switch (K) {
-    case 3: return emu_gen_k<3>(beta, polys, llr, n, f, v1, v2, mode, M, f0, rule, seed, out);
-    case 4: return emu_gen_k<4>(beta, polys, llr, n, f, v1, v2, mode, M, f0, rule, seed, out);
-    case 5: return emu_gen_k<5>(beta, polys, llr, n, f, v1, v2, mode, M, f0, rule, seed, out);
-    case 6: return emu_gen_k<6>(beta, polys, llr, n, f, v1, v2, mode, M, f0, rule, seed, out);
-    case 7: return emu_gen_k<7>(beta, polys, llr, n, f, v1, v2, mode, M, f0, rule, seed, out);
-  }
-  return -1;
-}

@@ -73,11 +73,37 @@ def test_create_validates_arguments(lib):
         rc, h = _create(lib, *args)
         assert rc == -1 and not h.value, args
         assert lib.vit_last_error()
-    # a valid code with no compiled kernel
+    # a valid code with no compiled kernel is decoded by the kernels that take
+    # the generators at run time; every valid code is supported
     rc, h = _create(lib, 7, 2, (0o165, 0o133), 0, 0)
-    assert rc == -2 and b"no kernel" in lib.vit_last_error()
+    assert rc == 0 and h.value
+    lib.vit_destroy(h)
+    for K in range(3, 10):
+        for beta in (2, 3, 4):
+            ok = (K - 1) * beta <= 32
+            polys = tuple((1 << (K - 1)) | (b + 1) for b in range(beta))
+            assert lib.vit_code_supported(K, beta, _u32(*polys)) == int(ok), (K, beta)
+            rc, h = _create(lib, K, beta, polys, 64, 10)
+            assert (rc == 0) == ok, (K, beta)
+            lib.vit_destroy(h)
     assert lib.vit_code_supported(7, 2, _u32(0o171, 0o133)) == 1
-    assert lib.vit_code_supported(7, 2, _u32(0o165, 0o133)) == 0
+    assert lib.vit_code_supported(7, 2, _u32(0o400, 0o133)) == 0
+
+
+def test_runtime_code_workspace_and_no_parallel_traceback(lib):
+    """A code without a compiled kernel: one warp per tile, max(S/32, 1)
+    decision words per stage, windows rounded up to 32 stages; the parallel
+    traceback needs a compiled kernel."""
+    lib.vit_set_parallel_traceback.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64]
+    for K, polys, R in ((8, (0o247, 0o371), 4), (9, (0o457, 0o755), 8), (5, (0o27, 0o31), 1)):
+        rc, h = _create(lib, K, 2, polys, 1024, 48)
+        assert rc == 0
+        n = 100_000
+        tiles = (n + 1023) // 1024
+        want = tiles * ((1120 + 31) // 32 * 32) * R * 4
+        assert lib.vit_decode_workspace(h, n) == (want + 255) // 256 * 256
+        assert lib.vit_set_parallel_traceback(h, 32, 0, 0) == -2
+        lib.vit_destroy(h)
 
 
 def test_counts_and_workspace(lib):

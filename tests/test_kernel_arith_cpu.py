@@ -102,46 +102,3 @@ def test_parallel_traceback_lane_routine_matches_oracle(emu, fn, code):
         f_(x.ctypes.data, n, f, v1, v2, mode, M, f0, rule, seed, out.ctypes.data)
         np.testing.assert_array_equal(synth.unpack_bits(out, nout), want[:nout], err_msg=f"case {i}")
 
-
-def _random_code(g, K, beta):
-    """Generators drawn uniformly from the nonzero K-bit words (taps on the
-    current and the oldest input are not required)."""
-    return tuple(int(x) for x in g.integers(1, 1 << K, size=beta))
-
-
-@pytest.mark.parametrize("K", [3, 4, 5, 6, 7])
-@pytest.mark.parametrize("beta", [2, 3, 4])
-def test_runtime_code_lane_routine_matches_oracle(emu, K, beta):
-    """The lane routine for codes known only at run time (branch signs from a
-    table built from the generators) on random generator sets, serial and
-    parallel traceback, against the oracle bit for bit."""
-    g = synth.rng(1000 + 10 * K + beta)
-    f_ = emu.emu_gen
-    f_.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
-                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
-                   ctypes.c_uint64, ctypes.c_void_p]
-    M = 2 * (K - 1) * 127 * beta + 1
-    for trial in range(3):
-        polys = _random_code(g, K, beta)
-        p = np.asarray(polys, dtype=np.uint32)
-        for i, (n, f, v, mode, f0) in enumerate([(3000, 64, 20, 0, 0), (2500, 0, 0, 1, 0), (64 * 70 + 9, 64, 9, 2, 0),
-                                                 (4000, 256, 30, 0, 32)]):
-            tail = K - 1 if mode == 1 else 0
-            s = synth.make_stream(lambda x: oracle.encode(K, beta, polys, x), beta, n, 1.0 + i, seed=trial * 10 + i,
-                                  tail=tail)
-            if f0:
-                want = oracle.viterbi_blocked_pt(K, beta, polys, s.llr, f, v, v, f0, mode=mode)
-            else:
-                want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v, mode)
-            nout = n - tail
-            out = np.zeros((nout + 7) // 8 + 1, np.uint8)
-            x = np.ascontiguousarray(s.llr, dtype=np.int8)
-            assert f_(K, beta, p.ctypes.data, x.ctypes.data, n, f, v, v, mode, M, f0, 0, 0, out.ctypes.data) == 0
-            np.testing.assert_array_equal(synth.unpack_bits(out, nout), want[:nout],
-                                          err_msg=f"K={K} beta={beta} polys={[oct(q) for q in polys]} case {i}")
-        # saturated LLRs: the widest spread the renormalisation must hold
-        llr = np.where(g.random((6000, beta)) < 0.5, -127, 127).astype(np.int8)
-        want = oracle.viterbi_blocked(K, beta, polys, llr, 512, 40, 40, 0)
-        out = np.zeros(6000 // 8 + 1, np.uint8)
-        assert f_(K, beta, p.ctypes.data, llr.ctypes.data, 6000, 512, 40, 40, 0, M, 0, 0, 0, out.ctypes.data) == 0
-        np.testing.assert_array_equal(synth.unpack_bits(out, 6000), want)
