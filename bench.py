@@ -468,6 +468,92 @@ def mixed_batch_leg(vit, torch, device, steps):
     }
 
 
+METRIC_WORKLOAD = ("1024 zero-terminated frames x (2048 + 6) stages, K=7 r1/2 (171,133), FP32 LLRs "
+                   "L = 2y/sigma^2 at Eb/N0 2 dB; best-path metric (hard) and log-sum-exp (tau 0.5, 1, 2), "
+                   "forward and backward, state metrics checkpointed every 64 stages")
+
+
+def metric_leg(vit, torch, device, steps, fp_rates, sm_mhz):
+    """The differentiable path metric at its workload size: forward and
+    backward time per tau, frames/s, and the achieved rate of the unit that
+    bounds each form (FP32 adds/max for the hard form, MUFU ex2/lg2 for the
+    log-sum-exp form) against the measured per-SM instruction rates."""
+    from paper_2011_09337_gb300 import synth
+    F, n_info, C = 1024, 2048, 64
+    n = n_info + K - 1
+    g = synth.rng(3)
+    msg = np.zeros((F, n), np.uint8)
+    msg[:, :n_info] = g.integers(0, 2, size=(F, n_info), dtype=np.uint8)
+    code = vit.Code(K, BETA, POLYS, mode=vit.TERMINATED)
+    coded = vit.encode(code, torch.from_numpy(msg.reshape(-1)).to(device)).cpu().numpy().astype(np.float64)
+    sigma = synth.noise_sigma(2.0, 1.0 / BETA)
+    y = (1.0 - 2.0 * coded) + sigma * g.standard_normal(coded.shape)
+    x = torch.from_numpy((2.0 * y / sigma ** 2).astype(np.float32).reshape(F, n, BETA)).to(device)
+    S = 1 << (K - 1)
+    state_stages = F * n * S
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    out = {"workload": METRIC_WORKLOAD, "frames": F, "stages_per_frame": n, "C": C}
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for tau in (0.0, 0.5, 1.0, 2.0):
+        xr = x.clone().requires_grad_(True)
+        for _ in range(2):
+            m = vit.path_metric(xr, code, tau, C)
+            (gx,) = torch.autograd.grad(m.sum(), xr)
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(steps):
+            m = vit.path_metric(xr, code, tau, C)
+        ev[1].record()
+        torch.cuda.synchronize()
+        fwd_ms = ev[0].elapsed_time(ev[1]) / steps
+        ev[0].record()
+        for _ in range(steps):
+            (gx,) = torch.autograd.grad(m.sum(), xr, retain_graph=True)
+        ev[1].record()
+        torch.cuda.synchronize()
+        bwd_ms = ev[0].elapsed_time(ev[1]) / steps
+        key = "hard" if tau == 0.0 else f"tau_{tau:g}"
+        r = {"fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "frames_per_s": F / ((fwd_ms + bwd_ms) * 1e-3),
+             "grad_finite": bool(torch.isfinite(gx).all().item())}
+        if tau == 0.0:
+            # 4 FP32 ops per state per stage (2 adds, compare, select) in the forward pass
+            peak = max(fp_rates["fadd"], fp_rates["fmax"]) * 32 * sms * sm_mhz * 1e6
+            ach = 4.0 * state_stages / (fwd_ms * 1e-3)
+            r["roofline_fwd"] = {"bound": "fp32", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                                 "frac": ach / peak, "ops": "4 FP32 ops per state per stage"}
+        else:
+            # one exp and one log per state per stage in the forward pass; the
+            # backward recomputes the forward (2), runs the beta recursion (2)
+            # and forms two branch posteriors (2 exp)
+            peak = min(fp_rates["ex2"], fp_rates["lg2"]) * 32 * sms * sm_mhz * 1e6
+            for leg, mufu, ms in (("fwd", 2.0, fwd_ms), ("bwd", 6.0, bwd_ms)):
+                ach = mufu * state_stages / (ms * 1e-3)
+                r[f"roofline_{leg}"] = {"bound": "mufu", "achieved": ach / 1e12, "peak": peak / 1e12,
+                                        "unit": "Tops/s", "frac": ach / peak,
+                                        "ops": f"{mufu:g} MUFU ops per state per stage"}
+        out[key] = r
+        del xr, m, gx
+    return out
+
+
+def metric_cpu_baseline():
+    """The FP64 oracle on the finite-difference subset (8 frames x (64 + 6)
+    stages): metric and gradient, hard and log-sum-exp (tau = 1)."""
+    import oracle
+    from paper_2011_09337_gb300 import synth
+    _, llr = synth.float_frames(lambda x: oracle.encode(K, BETA, POLYS, x), BETA, K, 8, 64, 2.0, seed=3)
+    x = llr.astype(np.float64)
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 2.0:
+        oracle.metric_hard(K, BETA, POLYS, x)
+        oracle.metric_lse(K, BETA, POLYS, x, 1.0)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": 8 / dt, "unit": "frames/s (hard + lse, fwd + grad)", "cores": 1, "kind": "oracle",
+            "sample": "8 frames x 70 stages, FP64, metric and gradient of the hard and tau = 1 forms, one thread"}
+
+
 LARGE_WORKLOAD = ("2^26-bit streams: K=9 r1/2 (561,753) f=2048 v=96; K=7 (171,133) punctured to r3/4 "
                   "[110;101] f=2048 v=64; K=9 punctured to r3/4 f=2048 v=96; int8 LLRs at Eb/N0 4 dB")
 
@@ -540,6 +626,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-code batch leg")
     ap.add_argument("--no-large", action="store_true", help="skip the 2^26-bit stream leg")
     ap.add_argument("--no-pt", action="store_true", help="skip the parallel-traceback leg")
+    ap.add_argument("--no-metric", action="store_true", help="skip the differentiable path-metric leg")
     ap.add_argument("--profile", action="store_true",
                     help="build the workload with --streams streams, run the planned batch twice and exit "
                          "(the target of the ncu captures)")
@@ -672,6 +759,12 @@ def main():
     frame = frame_latency_leg(vit, torch, dev, args.steps)
     mixed = None if args.no_mixed else mixed_batch_leg(vit, torch, dev, args.steps)
     large = None if args.no_large else large_streams_leg(vit, torch, dev, max(3, args.steps // 4))
+    fp_rates = fp_peak_leg(vit, dev)
+    sm_max_ = _peaks()[0]
+    metric = None
+    if not args.no_metric:
+        metric = metric_leg(vit, torch, dev, max(3, args.steps // 4), fp_rates, sm_max_)
+        metric["fp_rates_warp_instr_per_clk_sm"] = fp_rates
 
     if rank != 0:
         if world > 1:
@@ -716,6 +809,7 @@ def main():
         "frame_latency": frame,
         "batch_mixed": mixed,
         "large_streams": large,
+        "metric_leg": metric,
         "ber_6db": ber6,
     }
     if clocks.get("sm_mhz"):
@@ -725,6 +819,8 @@ def main():
         v, cores, sample, v1 = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": v, "unit": "Mbit/s", "cores": cores, "kind": "oracle", "sample": sample,
                                 "single_core": {"value": v1, "unit": "Mbit/s", "sample": "4 tiles on 1 thread"}}
+        if metric is not None:
+            metric["cpu_baseline"] = metric_cpu_baseline()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

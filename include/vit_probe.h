@@ -40,8 +40,9 @@ enum {
  * given stream (cudaStream_t as void*, NULL = legacy default stream), then
  * synchronises the stream.  Outputs (host pointers):
  *   warp_instr_per_clk_sm: warp-level instructions of that class retired per
- *                          SM clock cycle per SM (from each CTA's clock64
- *                          span, averaged over CTAs),
+ *                          SM clock cycle per SM: the instructions of the CTAs
+ *                          that ran on each SM over that SM's clock64 span
+ *                          (first CTA start to last CTA end), summed over SMs,
  *   ms:                    wall time of the launch (CUDA events),
  *   sms:                   the device's multiprocessor count.
  * ctas_per_sm in [1, 32], warps in [1, 32], iters in [1, 1<<20]; a grid

@@ -133,6 +133,98 @@ def table_iii(K: int, beta: int, polys: Sequence[int], ebn0_db: float, f0s: Sequ
     return res
 
 
+def bound_ebn0_at(K: int, beta: int, polys: Sequence[int], target: float, rate: float | None = None) -> float:
+    """Eb/N0 (dB) at which the union bound equals `target` (bisection; the
+    bound falls monotonically with Eb/N0)."""
+    lo, hi = -2.0, 15.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if union_bound(K, beta, polys, mid, rate) > target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def ebn0_at(points: Sequence[tuple[float, float]], target: float) -> float | None:
+    """Eb/N0 at which a measured BER curve crosses `target`: linear in
+    log10(BER) between the two measured points around the crossing; None if
+    the points do not bracket it."""
+    pts = sorted(p for p in points if p[1] > 0)
+    for (e0, b0), (e1, b1) in zip(pts, pts[1:]):
+        if b0 >= target >= b1:
+            if b0 == b1:
+                return e0
+            t = (math.log10(b0) - math.log10(target)) / (math.log10(b0) - math.log10(b1))
+            return e0 + t * (e1 - e0)
+    return None
+
+
+def curve(code: "vit.Code", target: float, ebn0s: Sequence[float], nbits: int, seed: int = 1):
+    """BER at increasing Eb/N0 until it is below target / 3 (a measured
+    BER under 100 / nbits is not used).  Returns [(Eb/N0, BER)]."""
+    pts = []
+    for e in ebn0s:
+        b = ber(code, e, nbits, seed=seed)
+        pts.append((e, b))
+        if b < target / 3 or b * nbits < 100:
+            break
+    return pts
+
+
+GAP_TARGET = 1e-4
+GAP_EBN0 = (2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 5.5, 6.0, 6.5)
+
+
+def gap_db(code: "vit.Code", K: int, beta: int, polys: Sequence[int], ref_ebn0: float, nbits: int,
+           target: float = GAP_TARGET):
+    """The paper's BER metric (Sec. "BER Performance"): how much more Eb/N0
+    the decoder needs than a reference curve to reach the target BER, here
+    both the code's union bound and a measured reference decoder.
+    Returns (gap to the union bound, gap to the reference, points)."""
+    pts = curve(code, target, GAP_EBN0, nbits)
+    e = ebn0_at(pts, target)
+    if e is None:
+        return None, None, pts
+    return e - bound_ebn0_at(K, beta, polys, target), e - ref_ebn0, pts
+
+
+def reference_ebn0(K: int, beta: int, polys: Sequence[int], nbits: int, target: float = GAP_TARGET) -> float:
+    """Eb/N0 at which the tiled decoder with a very long overlap (f = 2048,
+    v1 = v2 = 256: the traceback has merged with the maximum-likelihood path
+    long before it reaches the emitted stages) reaches the target BER."""
+    code = vit.Code(K, beta, polys, f=2048, v=256)
+    return ebn0_at(curve(code, target, GAP_EBN0, nbits), target)
+
+
+def table_ii_gaps(K, beta, polys, fs, v2s, v1=21, nbits=1 << 24, target=GAP_TARGET):
+    """Table II: dB gap of the serial-traceback decoder for every (f, v2)."""
+    ref = reference_ebn0(K, beta, polys, nbits, target)
+    out = {"target_ber": target, "nbits_per_point": nbits, "v1": v1, "reference_ebn0": ref,
+           "bound_ebn0": bound_ebn0_at(K, beta, polys, target), "cells": {}}
+    for f in fs:
+        for v2 in v2s:
+            code = vit.Code(K, beta, polys, f=f, v1=v1, v2=v2)
+            gb, gr, pts = gap_db(code, K, beta, polys, ref, nbits, target)
+            out["cells"][f"f={f},v2={v2}"] = {"f": f, "v2": v2, "gap_to_union_bound_db": gb,
+                                              "gap_to_reference_db": gr, "points": pts}
+    return out
+
+
+def table_iii_gaps(K, beta, polys, f0s, v2s, f=296, v1=21, rule=0, nbits=1 << 24, target=GAP_TARGET):
+    """Table III: dB gap of the parallel-traceback decoder for every (f0, v2)."""
+    ref = reference_ebn0(K, beta, polys, nbits, target)
+    out = {"target_ber": target, "nbits_per_point": nbits, "f": f, "v1": v1, "rule": rule, "reference_ebn0": ref,
+           "bound_ebn0": bound_ebn0_at(K, beta, polys, target), "cells": {}}
+    for f0 in f0s:
+        for v2 in v2s:
+            code = vit.Code(K, beta, polys, f=f, v1=v1, v2=v2, pt_f0=f0, pt_rule=rule, pt_seed=7)
+            gb, gr, pts = gap_db(code, K, beta, polys, ref, nbits, target)
+            out["cells"][f"f0={f0},v2={v2}"] = {"f0": f0, "v2": v2, "gap_to_union_bound_db": gb,
+                                                "gap_to_reference_db": gr, "points": pts}
+    return out
+
+
 def _print_grid(title, res, rows, cols, rname, cname):
     print(title)
     print(f"{rname:>6s} \\ {cname:<4s}" + "".join(f"{c:>10d}" for c in cols))
@@ -140,13 +232,39 @@ def _print_grid(title, res, rows, cols, rname, cname):
         print(f"{r:>11d}" + "".join(f"{res[(r, c)]:10.2e}" for c in cols))
 
 
+def _print_gaps(title, tab, rows, cols, rkey, ckey):
+    print(title)
+    print(f"{ckey:>6s} \\ {rkey:<4s}" + "".join(f"{r:>9d}" for r in rows))
+    for c in cols:
+        vals = []
+        for r in rows:
+            g = tab["cells"][f"{rkey}={r},{ckey}={c}"]["gap_to_union_bound_db"]
+            vals.append(f"{g:9.3f}" if g is not None else f"{'-':>9s}")
+        print(f"{c:>11d}" + "".join(vals))
+
+
 if __name__ == "__main__":
     import argparse
+    import json
     from . import synth
     ap = argparse.ArgumentParser()
     ap.add_argument("--ebn0", type=float, default=3.0)
     ap.add_argument("--bits", type=int, default=1 << 22)
+    ap.add_argument("--gaps", metavar="JSON", help="compute the dB-gap grids of Tables II and III and write them")
     a = ap.parse_args()
+    if a.gaps:
+        K, beta, polys = synth.CODE_K7_R12
+        t2 = table_ii_gaps(K, beta, polys, [32, 64, 128, 256, 512], [10, 20, 30, 40], nbits=a.bits)
+        t3 = table_iii_gaps(K, beta, polys, [8, 16, 24, 32, 40, 48, 56], [25, 30, 35, 40, 45], nbits=a.bits)
+        t3r = table_iii_gaps(K, beta, polys, [32], [25, 35, 45], rule=1, nbits=a.bits)
+        _print_gaps("Table II: dB gap to the union bound at BER 1e-4 (columns f, rows v2)", t2,
+                    [32, 64, 128, 256, 512], [10, 20, 30, 40], "f", "v2")
+        _print_gaps("Table III: dB gap, parallel traceback, f=296 (columns f0, rows v2)", t3,
+                    [8, 16, 24, 32, 40, 48, 56], [25, 30, 35, 40, 45], "f0", "v2")
+        with open(a.gaps, "w") as fh:
+            json.dump({"code": "K=7 (171,133) r1/2, int8 LLRs x16, BPSK/AWGN, STREAM",
+                       "table_ii": t2, "table_iii": t3, "table_iii_random_start": t3r}, fh, indent=1)
+        raise SystemExit(0)
     K, beta, polys = synth.CODE_K7_R12
     print("union bound, K=7 (171,133):",
           ", ".join(f"{e} dB: {union_bound(K, beta, polys, e):.2e}" for e in (2, 3, 4, 5, 6)))

@@ -61,7 +61,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ float bm(const uint8_t* aout, int R, const float* l, int beta) {
   const uint32_t o = aout[R];
   float d = 0.f;
-  for (int b = 0; b < beta; b++) d += ((o >> b) & 1u) ? -l[b] : l[b];
+  #pragma unroll
+  for (int b = 0; b < 4; b++)
+    if (b < beta) d += ((o >> b) & 1u) ? -l[b] : l[b];
   return d;
 }
 
@@ -75,20 +77,26 @@ struct Smem {
 __device__ void setup_aout(Smem& sm, const MArgs& a) {
   for (int R = threadIdx.x; R < (1 << a.K); R += blockDim.x) {
     uint32_t o = 0;
-    for (int b = 0; b < a.beta; b++) o |= (uint32_t)(__popc(a.polys[b] & (uint32_t)R) & 1) << b;
+    #pragma unroll
+    for (int b = 0; b < 4; b++)
+      if (b < a.beta) o |= (uint32_t)(__popc(a.polys[b] & (uint32_t)R) & 1) << b;
     sm.aout[R] = (uint8_t)o;
   }
   __syncthreads();
 }
 
-// One forward stage over the states of this lane: reads cur, writes nxt
-// (normalised), returns the normaliser.  hard: also the decision ballots.
+// One forward stage over the SPL states of this lane (SPL = a.spl, a
+// template parameter so the per-lane arrays stay in registers): reads cur,
+// writes nxt (normalised), returns the normaliser.  hard: also the decision
+// ballots.
+template <int SPL>
 __device__ float fwd_stage(const MArgs& a, const Smem& sm, const float* cur, float* nxt, const float* l, int lane,
                            uint32_t* dec) {
   const int S = a.S;
-  float v[kMaxS / 32];
+  float v[SPL];
   float mx = -INFINITY;
-  for (int k = 0; k < a.spl; k++) {
+#pragma unroll
+  for (int k = 0; k < SPL; k++) {
     const int j = lane + 32 * k;
     float r = -INFINITY;
     bool d = false;
@@ -109,7 +117,8 @@ __device__ float fwd_stage(const MArgs& a, const Smem& sm, const float* cur, flo
   }
   mx = warp_max(mx);
   if (mx == -INFINITY) mx = 0.f;
-  for (int k = 0; k < a.spl; k++) {
+#pragma unroll
+  for (int k = 0; k < SPL; k++) {
     const int j = lane + 32 * k;
     if (j < S) nxt[j] = v[k] - mx;
   }
@@ -117,6 +126,7 @@ __device__ float fwd_stage(const MArgs& a, const Smem& sm, const float* cur, flo
   return mx;
 }
 
+template <int SPL>
 __global__ void __launch_bounds__(kWarps * 32) metric_fwd_kernel(const MArgs a) {
   __shared__ Smem sm;
   setup_aout(sm, a);
@@ -133,7 +143,9 @@ __global__ void __launch_bounds__(kWarps * 32) metric_fwd_kernel(const MArgs a) 
   double off = 0.0;
   for (int64_t t = 0; t < a.n; t++) {
     float l[4];
-    for (int b = 0; b < a.beta; b++) l[b] = llr[t * a.beta + b];
+    #pragma unroll
+    for (int b = 0; b < 4; b++)
+      if (b < a.beta) l[b] = llr[t * a.beta + b];
     const float* cur = (t & 1) ? b1 : b0;
     float* nxt = (t & 1) ? b0 : b1;
     if (a.tau > 0.f) {
@@ -141,14 +153,15 @@ __global__ void __launch_bounds__(kWarps * 32) metric_fwd_kernel(const MArgs a) 
         float* ck = (float*)ws + (t / a.C) * S;
         for (int j = lane; j < S; j += 32) ck[j] = cur[j];
       }
-      off += (double)fwd_stage(a, sm, cur, nxt, l, lane, nullptr);
+      off += (double)fwd_stage<SPL>(a, sm, cur, nxt, l, lane, nullptr);
     } else {
-      uint32_t dec[kMaxS / 32];
-      off += (double)fwd_stage(a, sm, cur, nxt, l, lane, dec);
+      uint32_t dec[SPL];
+      off += (double)fwd_stage<SPL>(a, sm, cur, nxt, l, lane, dec);
       uint32_t* dw = (uint32_t*)ws + t * ((S + 31) / 32);
       if (lane < (S + 31) / 32) {
         uint32_t x = 0;
-        for (int k = 0; k < a.spl; k++)
+#pragma unroll
+        for (int k = 0; k < SPL; k++)
           if (k == lane) x = dec[k];
         dw[lane] = (S < 32) ? (x & ((1u << S) - 1u)) : x;
       }
@@ -188,13 +201,16 @@ __global__ void __launch_bounds__(kWarps * 32) metric_bwd_hard_kernel(const MArg
     __syncwarp();
     for (int64_t t = lo + lane; t < hi; t += 32) {
       const uint32_t o = sm.aout[sm.path[w][t - lo]];
-      for (int b = 0; b < a.beta; b++) grad[t * a.beta + b] = ((o >> b) & 1u) ? -g : g;
+      #pragma unroll
+      for (int b = 0; b < 4; b++)
+        if (b < a.beta) grad[t * a.beta + b] = ((o >> b) & 1u) ? -g : g;
     }
     __syncwarp();
   }
 }
 
 // soft backward: beta recursion from the end; alpha recomputed per segment
+template <int SPL>
 __global__ void __launch_bounds__(kWarps * 32) metric_bwd_soft_kernel(const MArgs a) {
   __shared__ Smem sm;
   setup_aout(sm, a);
@@ -221,19 +237,24 @@ __global__ void __launch_bounds__(kWarps * 32) metric_bwd_soft_kernel(const MArg
     __syncwarp();
     for (int64_t t = t0; t < t1 - 1; t++) {
       float l[4];
-      for (int b = 0; b < a.beta; b++) l[b] = llr[t * a.beta + b];
-      fwd_stage(a, sm, seg + (t - t0) * S, seg + (t - t0 + 1) * S, l, lane, nullptr);
+      #pragma unroll
+      for (int b = 0; b < 4; b++)
+        if (b < a.beta) l[b] = llr[t * a.beta + b];
+      fwd_stage<SPL>(a, sm, seg + (t - t0) * S, seg + (t - t0 + 1) * S, l, lane, nullptr);
     }
     __syncwarp();
     for (int64_t t = t1 - 1; t >= t0; t--) {
       float l[4];
-      for (int b = 0; b < a.beta; b++) l[b] = llr[t * a.beta + b];
+      #pragma unroll
+      for (int b = 0; b < 4; b++)
+        if (b < a.beta) l[b] = llr[t * a.beta + b];
       const float* al = seg + (t - t0) * S;   // alpha entering stage t
       const float* be = cur ? bb1 : bb0;       // beta leaving stage t
       float* bn = cur ? bb0 : bb1;
-      float u[kMaxS / 32][2], p[kMaxS / 32][2];
+      float u[SPL][2], p[SPL][2];
       float mx = -INFINITY, bmx = -INFINITY;
-      for (int k = 0; k < a.spl; k++) {
+#pragma unroll
+      for (int k = 0; k < SPL; k++) {
         const int i = lane + 32 * k;
         for (int in = 0; in < 2; in++) {
           u[k][in] = -INFINITY;
@@ -253,19 +274,24 @@ __global__ void __launch_bounds__(kWarps * 32) metric_bwd_soft_kernel(const MArg
       bmx = warp_max(bmx);
       if (bmx == -INFINITY) bmx = 0.f;
       float z = 0.f, gb[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int k = 0; k < a.spl; k++) {
+#pragma unroll
+      for (int k = 0; k < SPL; k++) {
         const int i = lane + 32 * k;
         if (i >= S) continue;
         for (int in = 0; in < 2; in++) {
           const float q = (p[k][in] == -INFINITY) ? 0.f : __expf((p[k][in] - mx) / tau);
           z += q;
           const uint32_t o = sm.aout[(in << (K - 1)) | i];
-          for (int b = 0; b < a.beta; b++) gb[b] += ((o >> b) & 1u) ? -q : q;
+          #pragma unroll
+          for (int b = 0; b < 4; b++)
+            if (b < a.beta) gb[b] += ((o >> b) & 1u) ? -q : q;
         }
         bn[i] = lse2(u[k][0], u[k][1], tau) - bmx;
       }
       z = warp_sum(z);
-      for (int b = 0; b < a.beta; b++) gb[b] = warp_sum(gb[b]);
+      #pragma unroll
+      for (int b = 0; b < 4; b++)
+        if (b < a.beta) gb[b] = warp_sum(gb[b]);
       if (lane < a.beta) {
         float gv = 0.f;
         for (int b = 0; b < a.beta; b++)
@@ -332,7 +358,13 @@ int vit_metric_fwd(const vit_code* c, const float* llr, int nframes, int64_t n, 
   a.metric = metric_out;
   a.ws = (uint8_t*)ws;
   const unsigned grid = (unsigned)((nframes + kWarps - 1) / kWarps);
-  metric_fwd_kernel<<<grid, kWarps * 32, 0, (cudaStream_t)stream>>>(a);
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (a.spl) {
+    case 1: metric_fwd_kernel<1><<<grid, kWarps * 32, 0, s>>>(a); break;
+    case 2: metric_fwd_kernel<2><<<grid, kWarps * 32, 0, s>>>(a); break;
+    case 4: metric_fwd_kernel<4><<<grid, kWarps * 32, 0, s>>>(a); break;
+    default: metric_fwd_kernel<8><<<grid, kWarps * 32, 0, s>>>(a); break;
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return vit::set_error(VIT_ECUDA, "metric forward launch: %s", cudaGetErrorString(e));
   return VIT_OK;
@@ -351,9 +383,15 @@ int vit_metric_bwd(const vit_code* c, const float* llr, const float* grad_metric
   a.grad = grad_llr;
   a.ws = (uint8_t*)const_cast<void*>(ws);
   const unsigned grid = (unsigned)((nframes + kWarps - 1) / kWarps);
-  if (tau > 0.f)
-    metric_bwd_soft_kernel<<<grid, kWarps * 32, 0, (cudaStream_t)stream>>>(a);
-  else
+  cudaStream_t s = (cudaStream_t)stream;
+  if (tau > 0.f) {
+    switch (a.spl) {
+      case 1: metric_bwd_soft_kernel<1><<<grid, kWarps * 32, 0, s>>>(a); break;
+      case 2: metric_bwd_soft_kernel<2><<<grid, kWarps * 32, 0, s>>>(a); break;
+      case 4: metric_bwd_soft_kernel<4><<<grid, kWarps * 32, 0, s>>>(a); break;
+      default: metric_bwd_soft_kernel<8><<<grid, kWarps * 32, 0, s>>>(a); break;
+    }
+  } else
     metric_bwd_hard_kernel<<<grid, kWarps * 32, 0, (cudaStream_t)stream>>>(a);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return vit::set_error(VIT_ECUDA, "metric backward launch: %s", cudaGetErrorString(e));

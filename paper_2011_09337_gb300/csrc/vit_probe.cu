@@ -1,7 +1,11 @@
 // vit_probe.cu -- instruction-rate microbenchmark (include/vit_probe.h): the
 // measured peak that the decoder's roofline fraction is taken against.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "../../include/vit.h"
 #include "../../include/vit_probe.h"
@@ -65,7 +69,13 @@ __global__ void probe_kernel(int iters, uint32_t seed, long long* cycles, uint32
   }
   __syncthreads();
   const long long t1 = clock64();
-  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  if (threadIdx.x == 0) {
+    uint32_t smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    cycles[3 * blockIdx.x] = t0;
+    cycles[3 * blockIdx.x + 1] = t1;
+    cycles[3 * blockIdx.x + 2] = smid;
+  }
   uint32_t acc = 0;
 #pragma unroll
   for (int c = 0; c < kPairs; c++) acc ^= x[c] ^ y[c];
@@ -98,7 +108,7 @@ extern "C" int vit_probe_rate(int kind, int ctas_per_sm, int warps, int iters, v
   long long* d_cyc = nullptr;
   uint32_t* d_sink = nullptr;
   cudaEvent_t a = nullptr, b = nullptr;
-  e = cudaMalloc(&d_cyc, sizeof(long long) * grid);
+  e = cudaMalloc(&d_cyc, sizeof(long long) * 3 * grid);
   if (e == cudaSuccess) e = cudaMalloc(&d_sink, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -127,17 +137,31 @@ extern "C" int vit_probe_rate(int kind, int ctas_per_sm, int warps, int iters, v
   if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
   long long* h = nullptr;
   if (e == cudaSuccess && rc == VIT_OK) {
-    h = new long long[grid];
-    e = cudaMemcpy(h, d_cyc, sizeof(long long) * grid, cudaMemcpyDeviceToHost);
+    h = new long long[3 * (size_t)grid];
+    e = cudaMemcpy(h, d_cyc, sizeof(long long) * 3 * grid, cudaMemcpyDeviceToHost);
   }
   if (e != cudaSuccess && rc == VIT_OK) rc = vit::set_error(VIT_ECUDA, "probe: %s", cudaGetErrorString(e));
   if (rc == VIT_OK) {
-    double mean = 0.0;
-    for (int i = 0; i < grid; i++) mean += (double)h[i];
-    mean /= grid;
-    // every thread retires iters * kSteps * kPairs * 2 instructions
-    const double warp_instr = (double)ctas_per_sm * warps * iters * kSteps * kPairs * 2.0;
-    *warp_instr_per_clk_sm = warp_instr / mean;
+    // per SM: the span from its first CTA's start to its last CTA's end (the
+    // block scheduler need not give every SM the same number of CTAs), and
+    // the instructions of its CTAs; every thread retires
+    // iters * kSteps * kPairs * 2 instructions
+    std::vector<long long> lo(1024, LLONG_MAX), hi(1024, LLONG_MIN);
+    std::vector<int> cnt(1024, 0);
+    for (int i = 0; i < grid; i++) {
+      const int sm = (int)(h[3 * i + 2] & 1023);
+      lo[sm] = std::min(lo[sm], h[3 * i]);
+      hi[sm] = std::max(hi[sm], h[3 * i + 1]);
+      cnt[sm]++;
+    }
+    const double per_cta = (double)warps * iters * kSteps * kPairs * 2.0;
+    double instr = 0.0, span = 0.0;
+    for (int sm = 0; sm < 1024; sm++)
+      if (cnt[sm] > 0) {
+        instr += cnt[sm] * per_cta;
+        span += (double)(hi[sm] - lo[sm]);
+      }
+    *warp_instr_per_clk_sm = instr / span;
     *ms = t;
     *sms = nsm;
   }

@@ -37,3 +37,27 @@ def test_sweep_trends(vit):
     stored = ber.table_iii(K, beta, polys, 2.5, f0s=[32], v2s=[9], rule=0, nbits=1 << 21)
     random = ber.table_iii(K, beta, polys, 2.5, f0s=[32], v2s=[9], rule=1, nbits=1 << 21)
     assert random[(32, 9)] > 2 * stored[(32, 9)]
+
+
+def test_gap_grids_follow_tables_ii_and_iii(vit):
+    """The dB gap to the union bound at BER 1e-4 (the paper's metric of
+    Tables II and III): a 10-stage right overlap costs visibly more than 20,
+    and beyond 20 little is gained (Sec. "BER Performance": v2 = 20
+    suffices); with the parallel traceback the gap falls as v2 grows and as
+    the subframes lengthen, and the recorded-argmax start beats the random
+    one."""
+    K, beta, polys = synth.CODE_K7_R12
+    n = 1 << 22
+    t2 = ber.table_ii_gaps(K, beta, polys, [256], [10, 20, 40], nbits=n)
+    g = {c["v2"]: c["gap_to_union_bound_db"] for c in t2["cells"].values()}
+    assert None not in g.values(), t2
+    assert g[10] > g[20] + 0.05, g
+    assert abs(g[20] - g[40]) < 0.1, g
+    t3 = ber.table_iii_gaps(K, beta, polys, [8, 56], [25, 45], nbits=n)
+    h = {(c["f0"], c["v2"]): c["gap_to_union_bound_db"] for c in t3["cells"].values()}
+    assert None not in h.values(), t3
+    assert h[(8, 25)] > h[(8, 45)] and h[(56, 25)] > h[(56, 45)], h
+    assert h[(8, 25)] > h[(56, 25)], h
+    t3r = ber.table_iii_gaps(K, beta, polys, [56], [25], rule=1, nbits=n)
+    r = next(iter(t3r["cells"].values()))["gap_to_union_bound_db"]
+    assert r is None or r > h[(56, 25)], (r, h)
