@@ -111,6 +111,20 @@ int vit_set_termination(vit_code* code, int mode);
 enum { VIT_PT_STORED = 0, VIT_PT_RANDOM = 1 };
 int vit_set_parallel_traceback(vit_code* code, int64_t f0, int rule, uint64_t seed);
 
+/*
+ * Decoder choice for vit_decode_ws / vit_decode / vit_decode_noalloc (batches
+ * always use the tile decoders).  VIT_DECODER_AUTO (initial): one warp per
+ * tile with the decisions in shared memory (Sec. "Unified Kernel": the
+ * survivors never leave the SM) for frames of at most 1024 tiles whose
+ * windows fit 6144 stages, else the tile decoder (two tiles per lane, 64 per
+ * warp, survivor words in the scratch slab).  VIT_DECODER_TILES always uses
+ * the tile decoder; VIT_DECODER_SHARED always uses the shared-memory decoder
+ * (any number of tiles; VIT_EUNSUPPORTED at decode time when a window exceeds
+ * 6144 stages or the code has no such decoder: K > 7 with compiled kernels).
+ */
+enum { VIT_DECODER_AUTO = 0, VIT_DECODER_TILES = 1, VIT_DECODER_SHARED = 2 };
+int vit_set_decoder(vit_code* code, int which);
+
 void vit_destroy(vit_code* code);
 
 /* Number of int8 LLRs the decoder reads for n trellis stages. */
@@ -121,7 +135,11 @@ int64_t vit_output_bits(const vit_code* code, int64_t n);
 
 /* --------------------------------------------------------------- decoding */
 
-/* Device scratch bytes vit_decode_ws needs for an n-stage frame. */
+/* Device scratch bytes vit_decode_ws needs for an n-stage frame on the
+ * current device.  The tile decoder's survivor slab holds one slot per warp
+ * task, but never more slots than warps of that decoder fit on the device at
+ * once: beyond one resident wave the warps stride over the tasks and reuse
+ * their slots, so the slab stops growing with n. */
 size_t vit_decode_workspace(const vit_code* code, int64_t n);
 
 /*

@@ -353,6 +353,14 @@ int vit_set_parallel_traceback(vit_code* c, int64_t f0, int rule, uint64_t seed)
   return VIT_OK;
 }
 
+int vit_set_decoder(vit_code* c, int which) {
+  if (int r = check_code(c)) return r;
+  if (which != VIT_DECODER_AUTO && which != VIT_DECODER_TILES && which != VIT_DECODER_SHARED)
+    return fail(VIT_EINVAL, "invalid decoder choice %d", which);
+  c->decoder = which;
+  return VIT_OK;
+}
+
 void vit_destroy(vit_code* c) { delete c; }
 
 int64_t vit_llr_count(const vit_code* c, int64_t n) {
@@ -380,12 +388,24 @@ static size_t slab_task_words(const vit_code* c, int64_t n) {
   return (size_t)Lr * c->entry->slab_lanes * c->entry->words;
 }
 
+// Slab slots of a single-frame decode with the tile decoder: 0 (one per
+// warp task) when every task's warp can be resident at once, else the
+// number of warps resident on the current device, which then stride over the
+// tasks and reuse their slots -- the slab stops growing with n after one
+// wave.  The parallel-traceback decoder keeps one slot per task.
+static int64_t slab_slots(const vit_code* c, int64_t tasks) {
+  if (c->pt_f0 > 0 || c->entry->resident == nullptr) return 0;
+  const int64_t r = c->entry->resident(kWarpsPerCta);
+  return (r > 0 && tasks > r) ? r : 0;
+}
+
 size_t vit_decode_workspace(const vit_code* c, int64_t n) {
   if (c == nullptr || n <= 0) return 0;
   const int64_t tiles = tile_count(n, c->f);
   const int64_t tpt = c->entry->tiles_per_task;
   const int64_t tasks = (tiles + tpt - 1) / tpt;
-  size_t bytes = align_up((size_t)tasks * slab_task_words(c, n) * 4);
+  const int64_t slots = slab_slots(c, tasks);
+  size_t bytes = align_up((size_t)(slots ? slots : tasks) * slab_task_words(c, n) * 4);
   if (c->period) bytes += align_up((size_t)n * c->beta);
   bytes += align_up((size_t)(tiles * pt_subframes(c, n)));
   return bytes;
@@ -397,9 +417,10 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
   const int64_t tpt = c->entry->tiles_per_task;
   const int64_t tasks = (tiles + tpt - 1) / tpt;
   const size_t tw = slab_task_words(c, n);
+  const int64_t slots = slab_slots(c, tasks);
   uint8_t* p = (uint8_t*)ws;
   uint32_t* slab = (uint32_t*)p;
-  p += align_up((size_t)tasks * tw * 4);
+  p += align_up((size_t)(slots ? slots : tasks) * tw * 4);
   const int8_t* dec_llr = llr;
   if (c->period) {
     int8_t* dep = (int8_t*)p;
@@ -438,6 +459,7 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
   a.ntasks = tasks;
   a.slab = slab;
   a.task_words = (int64_t)tw;
+  a.slots = slots;
   a.task_base = 0;
   for (int b = 0; b < c->beta; b++) a.polys[b] = c->polys[b];
   if (c->pt_f0 > 0) {
@@ -449,8 +471,14 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
   }
   LaunchFn launch = c->pt_f0 > 0 ? c->pt_launch : c->entry->launch;
   // few short tiles: one warp per tile decodes them with lower latency
-  if (c->pt_f0 == 0 && c->warp_launch != nullptr && tiles <= kWarpTileLimit && max_window(c, n) <= kWarpSmemStages)
+  const bool fits = c->warp_launch != nullptr && max_window(c, n) <= kWarpSmemStages;
+  if (c->pt_f0 == 0 && c->decoder == VIT_DECODER_AUTO && fits && tiles <= kWarpTileLimit) launch = c->warp_launch;
+  if (c->decoder == VIT_DECODER_SHARED) {
+    if (!fits || c->pt_f0 > 0)
+      return fail(VIT_EUNSUPPORTED, "the shared-memory decoder needs windows of at most %d stages, no parallel "
+                  "traceback and a code with such a decoder", (int)kWarpSmemStages);
     launch = c->warp_launch;
+  }
   cudaError_t e = launch(a, kWarpsPerCta, s);
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   return VIT_OK;

@@ -9,7 +9,8 @@ using C1 = Code<9, 2, 0561, 0753>;
 struct Reg {
   Reg() {
     static const CodeEntry e[] = {CodeEntry{C1::K, C1::BETA, {C1::poly(0), C1::poly(1), C1::poly(2), C1::poly(3)},
-                                            C1::WORDS, C1::U, 64 / C1::G, 32, 0, &launch_decode<C1>,
+                                            C1::WORDS, C1::U, 64 / C1::G, 32, 0,
+                                            &resident_warps<decode_tiles_kernel<C1, true>>, &launch_decode<C1>,
                                             &launch_k9_561_753_bytes}};
     register_codes(e, 1);
   }

@@ -30,8 +30,12 @@ struct KArgs {
   Tiling tl;
   uint32_t M;            // finite "-infinity" of a known start
   int64_t ntasks;        // warps with work
-  uint32_t* slab;        // survivor words, task_words per task
+  uint32_t* slab;        // survivor words, task_words per slot
   int64_t task_words;
+  // slab slots: 0 = one per task (task t uses slot t); otherwise the launch
+  // has at most `slots` warps, warp w decodes tasks w, w + W, ... (W = the
+  // launch's warps) and uses slot w, so the slab is bounded whatever n is
+  int64_t slots;
   int64_t task_base;     // first task index of this launch (for chunked launches)
   // parallel traceback (pt_f0 > 0): subframe length, start rule, SplitMix64
   // key, and one byte per subframe of every tile (pt_nsub per tile)
@@ -63,8 +67,8 @@ VIT_HD int64_t find_frame(const int64_t* tile0, int nframes, int64_t gt) {
 // lane's survivor slab.  e1f: each tile's emitted end before clipping to the
 // frame's output count (global tile indices in gt).
 template <class C>
-__device__ __forceinline__ void task_setup(const KArgs& a, int64_t task, int lane, Half (&hw)[2], int64_t (&gt)[2],
-                                           int64_t (&e1f)[2], int& Lw, int& mu, Slab& sl) {
+__device__ __forceinline__ void task_setup(const KArgs& a, int64_t task, int64_t slot, int lane, Half (&hw)[2],
+                                           int64_t (&gt)[2], int64_t (&e1f)[2], int& Lw, int& mu, Slab& sl) {
   constexpr int TPT = 64 / C::G;  // tiles per task
   const int pair = lane / C::G;
 #pragma unroll
@@ -98,17 +102,17 @@ __device__ __forceinline__ void task_setup(const KArgs& a, int64_t task, int lan
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-  sl = Slab{a.slab + task * a.task_words + lane * C::WORDS, 32 * C::WORDS};
+  sl = Slab{a.slab + slot * a.task_words + lane * C::WORDS, 32 * C::WORDS};
 }
 
 // Decodes warp task `task` of one code.
 template <class C, bool kWords = true>
-__device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane) {
+__device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int64_t slot, int lane) {
   Half hw[2];
   int64_t gt[2], e1f[2];
   int Lw, mu;
   Slab sl;
-  task_setup<C>(a, task, lane, hw, gt, e1f, Lw, mu, sl);
+  task_setup<C>(a, task, slot, lane, hw, gt, e1f, Lw, mu, sl);
   // word loads need every active tile's groups to start on 4-byte boundaries
   bool aligned = true;
 #pragma unroll
@@ -123,6 +127,21 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane)
     decode_pair_rot<C, kWords>(hw, Lw, mu, a.M, sl, lane, words_ok);
 }
 
+// Calls body(task, slot) for the warp tasks of this warp: one task per warp
+// in launch order (a.slots == 0), or tasks w, w + W, ... on slot w.
+template <class F>
+__device__ __forceinline__ void for_each_task(const KArgs& a, F&& body) {
+  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (a.slots == 0) {
+    const int64_t task = a.task_base + wid;
+    if (task < a.ntasks) body(task, task);  // warp-uniform
+    return;
+  }
+  if (wid >= a.slots) return;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t task = a.task_base + wid; task < a.ntasks; task += nw) body(task, wid);
+}
+
 // One warp per task, tasks in launch order.  kWords = false compiles the
 // byte-load path only (used for batches of short frames, where most groups
 // of a warp are loaded with masking anyway and the kernel with both paths
@@ -130,9 +149,7 @@ __device__ __forceinline__ void run_task(const KArgs& a, int64_t task, int lane)
 template <class C, bool kWords = true>
 __global__ void __maxnreg__((C::G > 1 && kWords) ? kMaxRegsRotWords : kMaxRegs) decode_tiles_kernel(const KArgs a) {
   const int lane = threadIdx.x & 31;
-  const int64_t task = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (task >= a.ntasks) return;  // warp-uniform
-  run_task<C, kWords>(a, task, lane);
+  for_each_task(a, [&](int64_t task, int64_t slot) { run_task<C, kWords>(a, task, slot, lane); });
 }
 
 // Persistent kernel over the tasks of two codes: each warp takes the next
@@ -152,7 +169,7 @@ struct MixArgs {
 // Out-of-line task bodies keep the two codes' register allocations apart.
 template <class C>
 __device__ __noinline__ void run_task_call(const KArgs a, int64_t task, int lane) {
-  run_task<C, (C::G == 1)>(a, task, lane);
+  run_task<C, (C::G == 1)>(a, task, task, lane);
 }
 
 template <class C0, class C1>
@@ -181,6 +198,7 @@ struct CodeEntry {
   int tiles_per_task;
   int slab_lanes;  // lanes whose survivor words one task stores per stage (32; 1 for one warp per tile)
   int generic;     // 1: patterns from the code's generators at run time
+  int64_t (*resident)(int warps);  // resident warps of `launch` on the current device
   cudaError_t (*launch)(const KArgs&, int warps, cudaStream_t);
   cudaError_t (*launch_bytes)(const KArgs&, int warps, cudaStream_t);  // byte loads only
 };
@@ -199,6 +217,11 @@ struct MixEntry {
 template <void (*kernel)(const KArgs)>
 cudaError_t launch_tasks(const KArgs& a, int warps, cudaStream_t s) {
   if (warps < 1 || warps > 8) warps = kWarpsPerCta;
+  if (a.slots > 0) {  // at most `slots` warps stride over the tasks
+    const int64_t need = a.ntasks - a.task_base < a.slots ? a.ntasks - a.task_base : a.slots;
+    kernel<<<(unsigned)((need + warps - 1) / warps), warps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   const int64_t maxc = (int64_t)1 << 30;
   for (int64_t t0 = a.task_base; t0 < a.ntasks; t0 += maxc * warps) {
     KArgs b = a;
@@ -210,6 +233,19 @@ cudaError_t launch_tasks(const KArgs& a, int warps, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Warps of `kernel` (CTAs of `warps` warps) resident at once on the current
+// device, or 0 when the device cannot be queried.
+template <void (*kernel)(const KArgs)>
+int64_t resident_warps(int warps) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, warps * 32, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (int64_t)sms * per_sm * warps;
 }
 
 template <class C>
@@ -250,8 +286,9 @@ constexpr LaunchFn bytes_launcher() {
 
 template <class C>
 constexpr CodeEntry make_entry() {
-  return CodeEntry{C::K, C::BETA, {C::poly(0), C::poly(1), C::poly(2), C::poly(3)}, C::WORDS, C::U,
-                   64 / C::G, 32, 0, &launch_decode<C>, bytes_launcher<C>()};
+  return CodeEntry{C::K,       C::BETA, {C::poly(0), C::poly(1), C::poly(2), C::poly(3)}, C::WORDS, C::U, 64 / C::G,
+                   32,         0,       &resident_warps<decode_tiles_kernel<C, true>>,    &launch_decode<C>,
+                   bytes_launcher<C>()};
 }
 
 #endif
@@ -297,6 +334,7 @@ struct vit_code {
   uint64_t pt_seed;
   vit::LaunchFn pt_launch;
   vit::LaunchFn warp_launch;  // warp-per-tile decoder, or nullptr
+  int decoder;                // VIT_DECODER_AUTO, _TILES or _SHARED
 };
 
 namespace vit {

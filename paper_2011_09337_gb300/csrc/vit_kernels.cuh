@@ -43,12 +43,12 @@ cudaError_t launch_warp(const KArgs& a, int, cudaStream_t s) {
 template <class C>
 __global__ void __launch_bounds__(256) decode_warp_gen_kernel(const KArgs a) {
   const int lane = threadIdx.x & 31;
-  const int64_t t = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (t >= a.ntasks) return;  // warp-uniform
-  const int64_t fi = (a.frames == nullptr) ? -1 : find_frame(a.tile0, a.nframes, t);
-  const Frame& fr = (fi < 0) ? a.f0 : a.frames[fi];
-  const int64_t b = (fi < 0) ? t : t - a.tile0[fi];
-  decode_tile_warp_gen<C>(make_half(fr, b, a.tl), a.M, a.slab + t * a.task_words, lane, a.polys);
+  for_each_task(a, [&](int64_t t, int64_t slot) {
+    const int64_t fi = (a.frames == nullptr) ? -1 : find_frame(a.tile0, a.nframes, t);
+    const Frame& fr = (fi < 0) ? a.f0 : a.frames[fi];
+    const int64_t b = (fi < 0) ? t : t - a.tile0[fi];
+    decode_tile_warp_gen<C>(make_half(fr, b, a.tl), a.M, a.slab + slot * a.task_words, lane, a.polys);
+  });
 }
 
 template <class C>
@@ -60,18 +60,18 @@ cudaError_t launch_warp_gen(const KArgs& a, int warps, cudaStream_t s) {
 // decisions per stage in the slab, windows rounded up to blocks of 32.
 template <class C>
 constexpr CodeEntry make_gen_entry() {
-  return CodeEntry{C::K, C::BETA, {0, 0, 0, 0}, C::S >= 32 ? C::S / 32 : 1, 32, 1, 1, 1, &launch_warp_gen<C>,
-                   &launch_warp_gen<C>};
+  return CodeEntry{C::K, C::BETA, {0, 0, 0, 0}, C::S >= 32 ? C::S / 32 : 1, 32, 1, 1, 1,
+                   &resident_warps<decode_warp_gen_kernel<C>>, &launch_warp_gen<C>, &launch_warp_gen<C>};
 }
 
 // Warp task of the tile decoder with the parallel traceback.
 template <class C>
-__device__ __forceinline__ void pt_task(const KArgs& a, int64_t task, int lane) {
+__device__ __forceinline__ void pt_task(const KArgs& a, int64_t task, int64_t slot, int lane) {
   Half hw[2];
   int64_t gt[2], e1f[2];
   int Lw, mu;
   Slab sl;
-  task_setup<C>(a, task, lane, hw, gt, e1f, Lw, mu, sl);
+  task_setup<C>(a, task, slot, lane, hw, gt, e1f, Lw, mu, sl);
   uint8_t* const st[2] = {hw[0].active ? a.pt_states + gt[0] * a.pt_nsub : nullptr,
                           hw[1].active ? a.pt_states + gt[1] * a.pt_nsub : nullptr};
   const PtParams pt{a.pt_f0, a.pt_rule, a.pt_seed};
@@ -88,9 +88,7 @@ __device__ __forceinline__ void pt_task(const KArgs& a, int64_t task, int lane) 
 template <class C>
 __global__ void __maxnreg__(kMaxRegs) decode_tiles_pt_kernel(const KArgs a) {
   const int lane = threadIdx.x & 31;
-  const int64_t task = a.task_base + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (task >= a.ntasks) return;  // warp-uniform
-  pt_task<C>(a, task, lane);
+  for_each_task(a, [&](int64_t task, int64_t slot) { pt_task<C>(a, task, slot, lane); });
 }
 
 template <class C>

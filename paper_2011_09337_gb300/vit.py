@@ -16,6 +16,7 @@ import torch
 from . import build_lib
 
 STREAM, TERMINATED, FREE_START = 0, 1, 2
+DECODER_AUTO, DECODER_TILES, DECODER_SHARED = 0, 1, 2
 BATCH_GRAPH, BATCH_PERSISTENT, BATCH_HOST = 1, 4, 8
 PT_STORED, PT_RANDOM = 0, 1
 
@@ -57,6 +58,7 @@ def load(path: str | None = None):
         "vit_code_supported": (i32, [i32, i32, vp]),
         "vit_set_parallel_traceback": (i32, [vp, i64, i32, ctypes.c_uint64]),
         "vit_hard_llr": (i32, [vp, i64, vp, vp]),
+        "vit_set_decoder": (i32, [vp, i32]),
     }
     optional = {
         "vit_batch_plan": (i32, [ctypes.POINTER(vp), vp, i32, i32]),
@@ -101,9 +103,10 @@ class Code:
     def __init__(self, K: int, beta: int, polys: Sequence[int], f: int = 0, v: int = 0,
                  v1: int | None = None, v2: int | None = None, mode: int = STREAM,
                  puncture: Sequence[Sequence[int]] | None = None, pt_f0: int = 0, pt_rule: int = 0,
-                 pt_seed: int = 0):
+                 pt_seed: int = 0, decoder: int = DECODER_AUTO):
         """pt_f0 > 0 selects the parallel traceback with subframes of pt_f0
-        stages (pt_rule: PT_STORED or PT_RANDOM, pt_seed: SplitMix64 key)."""
+        stages (pt_rule: PT_STORED or PT_RANDOM, pt_seed: SplitMix64 key);
+        decoder: DECODER_AUTO, DECODER_TILES or DECODER_SHARED (vit_set_decoder)."""
         L = load()
         self.K, self.beta, self.polys = K, beta, tuple(int(p) for p in polys)
         self.f = f
@@ -128,6 +131,8 @@ class Code:
         self.pt = (pt_f0, pt_rule, pt_seed)
         if pt_f0:
             _check(L.vit_set_parallel_traceback(h, pt_f0, pt_rule, pt_seed))
+        if decoder != DECODER_AUTO:
+            _check(L.vit_set_decoder(h, decoder))
 
     @property
     def handle(self):

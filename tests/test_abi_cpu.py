@@ -90,6 +90,17 @@ def test_create_validates_arguments(lib):
     assert lib.vit_code_supported(7, 2, _u32(0o400, 0o133)) == 0
 
 
+def test_decoder_choice_is_validated(lib):
+    lib.vit_set_decoder.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    rc, h = _create(lib, 7, 2, (0o171, 0o133), 1024, 48)
+    assert rc == 0
+    for which in (0, 1, 2):
+        assert lib.vit_set_decoder(h, which) == 0
+    assert lib.vit_set_decoder(h, 3) == -1
+    assert lib.vit_set_decoder(None, 0) == -1
+    lib.vit_destroy(h)
+
+
 def test_runtime_code_workspace_and_no_parallel_traceback(lib):
     """A code without a compiled kernel: one warp per tile, max(S/32, 1)
     decision words per stage, windows rounded up to 32 stages; the parallel

@@ -105,3 +105,42 @@ def test_tile_decoder_unaligned_llrs(vit, key, offset):
     want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v)
     got = _decode(vit, key, s.llr, n, f, v, v, oracle.STREAM, offset=offset)
     np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("key", ["k7", "k7r13", "k5", "k6asym"])
+def test_decoder_choice(vit, key):
+    """vit_set_decoder: the shared-memory warp-per-tile decoder on a frame of
+    more than 1024 tiles, the tile decoder on a frame of a few tiles; both
+    match the oracle.  A window longer than 6144 stages cannot use the
+    shared-memory decoder."""
+    K, beta, polys = CODES[key]
+    for n, f, v, which in ((9001, 8, 12, vit.DECODER_SHARED), (3000, 256, 20, vit.DECODER_TILES),
+                           (5000, 0, 0, vit.DECODER_TILES), (2049 * 16, 16, 30, vit.DECODER_SHARED)):
+        s = synth.make_stream(_enc(CODES[key]), beta, n, 2.0, seed=n + K)
+        c = vit.Code(K, beta, polys, f=f, v=v, decoder=which)
+        got = synth.unpack_bits(vit.decode(c, torch.from_numpy(s.llr.reshape(-1)).cuda(), n=n).cpu().numpy(), n)
+        np.testing.assert_array_equal(got, oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v),
+                                      err_msg=f"n={n} f={f} decoder={which}")
+    c = vit.Code(K, beta, polys, f=0, v=0, decoder=vit.DECODER_SHARED)
+    x = torch.zeros(7000 * beta, dtype=torch.int8, device="cuda")
+    with pytest.raises(vit.VitError):
+        vit.decode(c, x, n=7000)
+
+
+@pytest.mark.parametrize("key", ["k7", "k9"])
+def test_slab_slots_reused_beyond_one_wave(vit, key):
+    """A frame with more warp tasks than the tile decoder keeps resident: the
+    warps stride over the tasks and reuse their survivor-slab slots, so the
+    scratch stops growing with n, and the bits still match the oracle."""
+    K, beta, polys = CODES[key]
+    f, v = 8, 2 * (K - 1)
+    tpt = 64 if K <= 7 else 16
+    n = f * tpt * 3000 + 5  # 3000 warp tasks, more than any GB300 keeps resident
+    c = vit.Code(K, beta, polys, f=f, v=v)
+    per_task = ((f + 2 * v + 7) // 8 * 8) * 32 * 16
+    assert c.workspace_bytes(n) < 3000 * per_task
+    assert c.workspace_bytes(2 * n) == c.workspace_bytes(n)
+    s = synth.make_stream(_enc(CODES[key]), beta, n, 2.0, seed=K)
+    want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v)
+    got = _decode(vit, key, s.llr, n, f, v, v, oracle.STREAM)
+    np.testing.assert_array_equal(got, want)
