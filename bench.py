@@ -414,6 +414,32 @@ def parallel_traceback_leg(vit, torch, frames_llr, out, steps):
             "ms_per_step": ms, "bits_differing_from_serial_traceback": diff / nb}
 
 
+def shared_decoder_leg(vit, torch, frames_llr, ref_out, steps):
+    """The main workload decoded by the warp-per-tile decoder whose survivor
+    decisions stay in shared memory (Sec. "Unified Kernel": one warp per tile,
+    9 KB of decision words per 1120-stage window, nothing written to a slab),
+    one launch per stream, beside the tile decoder's survivor slab in HBM."""
+    code = vit.Code(K, BETA, POLYS, f=F, v=V, decoder=vit.DECODER_SHARED)
+    outs = [torch.zeros_like(o) for o in ref_out]
+    for _ in range(2):
+        for x, o in zip(frames_llr, outs):
+            vit.decode(code, x, NBITS, out=o)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        for x, o in zip(frames_llr, outs):
+            vit.decode(code, x, NBITS, out=o)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    same = all(torch.equal(o, r) for o, r in zip(outs, ref_out))
+    nb = NBITS * len(frames_llr)
+    return {"value": nb / (ms * 1e-3) / 1e6, "unit": "Mbit/s", "ms_per_step": ms, "matches_tile_decoder": same,
+            "launches_per_step": len(frames_llr),
+            "kernel": "decode_warp_kernel (one warp per tile, decisions in shared memory)"}
+
+
 def mixed_batch_leg(vit, torch, device, steps):
     from paper_2011_09337_gb300 import tune
 
@@ -777,6 +803,7 @@ def main():
     seq_ms = timed(seq_step, args.steps)
 
     pt = None if args.no_pt else parallel_traceback_leg(vit, torch, d_llr, d_out, args.steps)
+    shared = shared_decoder_leg(vit, torch, d_llr, d_out, max(3, args.steps // 4))
     frame = frame_latency_leg(vit, torch, dev, args.steps)
     mixed = None if args.no_mixed else mixed_batch_leg(vit, torch, dev, args.steps)
     large = None if args.no_large else large_streams_leg(vit, torch, dev, max(3, args.steps // 4))
@@ -827,6 +854,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": args.steps,
         "parallel_traceback": pt,
+        "shared_memory_decoder": shared,
         "frame_latency": frame,
         "batch_mixed": mixed,
         "large_streams": large,

@@ -179,6 +179,8 @@ VIT_HD uint32_t bmv(const StageBM<C>& bm, uint32_t c) {
 // and issues on the FMA pipe, leaving the ALU pipe to max, prmt and lop3).
 #if defined(__CUDACC__)
 static __constant__ uint32_t kOne = 1u;
+// multipliers -4..4 for y + c * x on the FMA pipe (index c + 4)
+static __constant__ uint32_t kSmall[9] = {0xfffffffcu, 0xfffffffdu, 0xfffffffeu, 0xffffffffu, 0u, 1u, 2u, 3u, 4u};
 #endif
 VIT_HD uint32_t add_on_fma(uint32_t x, uint32_t k) {
 #if defined(__CUDA_ARCH__)
@@ -187,6 +189,20 @@ VIT_HD uint32_t add_on_fma(uint32_t x, uint32_t k) {
   return r;
 #else
   return x + k;
+#endif
+}
+
+// y + c * x for a compile-time c in [-4, 4], as one multiply-add whose
+// multiplier comes from constant memory (so it issues on the FMA pipe).
+template <int c>
+VIT_HD uint32_t mad_small(uint32_t x, uint32_t y) {
+  static_assert(c >= -4 && c <= 4, "multiplier in [-4, 4]");
+#if defined(__CUDA_ARCH__)
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(kSmall[c + 4]), "r"(y));
+  return r;
+#else
+  return y + (uint32_t)c * x;
 #endif
 }
 
@@ -208,7 +224,7 @@ VIT_HD void stage_bm(const int (&lA)[C::BETA], const int (&lB)[C::BETA], StageBM
 
 // Survivor-word position of slot s (tile h adds 16).
 template <class C>
-VIT_HD int surv_word(int s) {
+VIT_CX int surv_word(int s) {
   return C::NS >= 16 ? (s >> 4) : 0;
 }
 template <class C>
@@ -228,21 +244,55 @@ VIT_HD int surv_pos(int s) {
   return (s & (C::HALFP - 1)) + ((s & C::HALFP) ? 8 : 0);
 }
 
+// Coefficient of magnitude D[i] in d(c10) - d(c11) - d(c00) + d(c01), with
+// d(c) = D[c] for patterns whose top bit is 0 and -D[~c] otherwise.
+template <class C>
+VIT_CX int bf_coef(uint32_t c00, uint32_t c01, uint32_t c10, uint32_t c11, int i) {
+  auto term = [](uint32_t c, int i) -> int {
+    const bool top = ((c >> (C::BETA - 1)) & 1u) != 0;
+    const uint32_t idx = top ? ((~c) & (uint32_t)(C::ND - 1)) : c;
+    return (idx == (uint32_t)i) ? (top ? -1 : 1) : 0;
+  };
+  return term(c10, i) - term(c11, i) - term(c00, i) + term(c01, i);
+}
+template <class C>
+VIT_CX int bf_nonzero(uint32_t c00, uint32_t c01, uint32_t c10, uint32_t c11) {
+  int n = 0;
+  for (int i = 0; i < C::ND; i++) n += bf_coef<C>(c00, c01, c10, c11, i) != 0 ? 1 : 0;
+  return n;
+}
+template <class C>
+VIT_CX int bf_index(uint32_t c00, uint32_t c01, uint32_t c10, uint32_t c11) {
+  for (int i = 0; i < C::ND; i++)
+    if (bf_coef<C>(c00, c01, c10, c11, i) != 0) return i;
+  return 0;
+}
+
 // One radix-2 butterfly (Eq. 3, Eq. 4): predecessors 2x (even) and 2x+1
 // (odd) of mi give successors x and x + S/2 in mo, with their decision words.
-template <class C>
-VIT_HD void butterfly(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const StageBM<C>& D, int x,
-                      uint32_t& E0, uint32_t& E1) {
+template <class C, int x>
+VIT_HD void butterfly(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const StageBM<C>& D, uint32_t& E0,
+                      uint32_t& E1) {
   constexpr int H = C::NS / 2;
-  const uint32_t i0 = 2u * (uint32_t)x;
-  const uint32_t c00 = C::aout(i0), c01 = C::aout(i0 | 1u);
-  const uint32_t c10 = C::aout(i0 | (uint32_t)C::S), c11 = C::aout(i0 | (uint32_t)C::S | 1u);
+  constexpr uint32_t i0 = 2u * (uint32_t)x;
+  constexpr uint32_t c00 = C::aout(i0), c01 = C::aout(i0 | 1u);
+  constexpr uint32_t c10 = C::aout(i0 | (uint32_t)C::S), c11 = C::aout(i0 | (uint32_t)C::S | 1u);
   const uint32_t x00 = add_bm<C>(mi[2 * x], D, c00), x01 = add_bm<C>(mi[2 * x + 1], D, c01);
   const uint32_t x10 = add_bm<C>(mi[2 * x], D, c10), x11 = add_bm<C>(mi[2 * x + 1], D, c11);
   E0 = x00 - x01 + 0x8000u;
   // x10 - x11 = (x00 - x01) + (d(c10) - d(c11) - d(c00) + d(c01)): the
-  // bracket is the same for every butterfly with these patterns this stage
-  E1 = add_on_fma(E0, bmv<C>(D, c10) - bmv<C>(D, c11) - bmv<C>(D, c00) + bmv<C>(D, c01));
+  // bracket is a sum of the stage's magnitudes D[i] with small integer
+  // coefficients; with one nonzero coefficient (every generator tapping the
+  // current and the oldest input) it is one multiply-add onto E0, otherwise
+  // the bracket is formed once per stage and added
+  constexpr int nz = bf_nonzero<C>(c00, c01, c10, c11);
+  if constexpr (nz == 1) {
+    constexpr int i = bf_index<C>(c00, c01, c10, c11);
+    constexpr int k = bf_coef<C>(c00, c01, c10, c11, i);
+    E1 = mad_small<k>(D.D[i], E0);
+  } else {
+    E1 = add_on_fma(E0, bmv<C>(D, c10) - bmv<C>(D, c11) - bmv<C>(D, c00) + bmv<C>(D, c01));
+  }
   mo[x] = vmaxu2(x00, x01);
   mo[x + H] = vmaxu2(x10, x11);
 }
@@ -255,35 +305,53 @@ VIT_HD void gather2(uint32_t (&w)[C::WORDS], int s, uint32_t Es, uint32_t Ep) {
   w[surv_word<C>(s)] |= t & (0x01010101u << (s & (C::HALFP - 1)));
 }
 
+// The same when the states of each survivor word arrive in increasing
+// position order: the word's first pair (position 0) initialises it, and each
+// later pair at position p keeps the word's bits below p of every byte and
+// takes the rest from the new sign bytes (one three-input select).
+template <class C, int s>
+VIT_HD void gather2_ordered(uint32_t (&w)[C::WORDS], uint32_t Es, uint32_t Ep) {
+  constexpr int p = s & (C::HALFP - 1);
+  constexpr int k = surv_word<C>(s);
+  const uint32_t t = prmt(Es, Ep, 0xFBD9u);
+  if constexpr (p == 0) {
+    w[k] = t;
+  } else {
+    constexpr uint32_t keep = 0x01010101u * ((1u << p) - 1u);
+    w[k] = (w[k] & keep) | (t & ~keep);
+  }
+}
+
 // One add-compare-select stage from mi to mo.  Butterflies are visited so
 // that the two states each prmt combines (s, s + HALFP) are finished
-// together, which keeps few decision words live.
+// together, which keeps few decision words live, and so that every survivor
+// word receives its positions in increasing order.
+template <class C, int x>
+VIT_HD void acs_from(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const StageBM<C>& D,
+                     uint32_t (&w)[C::WORDS]) {
+  constexpr int H = C::NS / 2;
+  constexpr int HP = C::HALFP;
+  if constexpr (x < H) {
+    if constexpr (H == HP) {
+      // the two successors of a butterfly are a prmt pair
+      uint32_t E0, E1;
+      butterfly<C, x>(mi, mo, D, E0, E1);
+      gather2_ordered<C, x>(w, E0, E1);
+    } else if constexpr ((x & HP) == 0) {
+      uint32_t Ea, Eb, Ec, Ed;  // successors x, x+H, x+HP, x+HP+H
+      butterfly<C, x>(mi, mo, D, Ea, Eb);
+      butterfly<C, x + HP>(mi, mo, D, Ec, Ed);
+      gather2_ordered<C, x>(w, Ea, Ec);
+      gather2_ordered<C, x + H>(w, Eb, Ed);
+    }
+    acs_from<C, x + 1>(mi, mo, D, w);
+  }
+}
+
 template <class C>
 VIT_HD void acs_stage(const uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const StageBM<C>& D,
                       uint32_t (&w)[C::WORDS]) {
-  constexpr int H = C::NS / 2;
-  constexpr int HP = C::HALFP;
-#pragma unroll
-  for (int k = 0; k < C::WORDS; k++) w[k] = 0u;
-  if constexpr (H == HP) {
-    // the two successors of a butterfly are a prmt pair
-#pragma unroll
-    for (int x = 0; x < H; x++) {
-      uint32_t E0, E1;
-      butterfly<C>(mi, mo, D, x, E0, E1);
-      gather2<C>(w, x, E0, E1);
-    }
-  } else {
-#pragma unroll
-    for (int x = 0; x < H; x++) {
-      if (x & HP) continue;
-      uint32_t Ea, Eb, Ec, Ed;  // successors x, x+H, x+HP, x+HP+H
-      butterfly<C>(mi, mo, D, x, Ea, Eb);
-      butterfly<C>(mi, mo, D, x + HP, Ec, Ed);
-      gather2<C>(w, x, Ea, Ec);
-      gather2<C>(w, x + H, Eb, Ed);
-    }
-  }
+  acs_from<C, 0>(mi, mo, D, w);
 }
 
 // Subtracts the metric of state 0 from every state (both tiles) and re-biases.
@@ -459,6 +527,35 @@ VIT_HD void pairs_from_words(const uint32_t (&w)[2][C::U * C::BETA / 4], int (&L
   }
 }
 
+// Branch magnitudes of stage u of a group straight from the group's words:
+// the prmt fields c_b = [l_B : l_A] (sign-extended halves) with bit 15
+// flipped are X_b = L_b + 2^15 in the integer encoding (the flip adds 2^15
+// when l_A >= 0 and turns the field's 2^16 - |l_A| into 2^15 - |l_A| when
+// l_A < 0), so D[c'] = sum_b (-1)^{c'_b} X_b - (sum_b (-1)^{c'_b}) 2^15.
+template <class C, int u>
+VIT_HD void bm_from_words(const uint32_t (&w)[2][C::U * C::BETA / 4], StageBM<C>& D) {
+  uint32_t X[C::BETA];
+#pragma unroll
+  for (int b = 0; b < C::BETA; b++) {
+    const int q = u * C::BETA + b;  // byte of the group
+    const int k = q >> 2, j = q & 3;
+    const uint32_t sel = (uint32_t)j | ((8u | (uint32_t)j) << 4) | ((4u + (uint32_t)j) << 8) |
+                         ((8u | (4u + (uint32_t)j)) << 12);
+    X[b] = prmt(w[0][k], w[1][k], sel) ^ 0x8000u;
+  }
+#pragma unroll
+  for (int c = 0; c < C::ND; c++) {
+    uint32_t acc = 0;
+    int nsum = 0;
+#pragma unroll
+    for (int b = 0; b < C::BETA; b++) {
+      acc = ((c >> b) & 1) ? acc - X[b] : acc + X[b];
+      nsum += ((c >> b) & 1) ? -1 : 1;
+    }
+    D.D[c] = acc - (uint32_t)nsum * 0x8000u;
+  }
+}
+
 template <class C>
 VIT_HD void bm_from_pairs(const int (&L)[C::BETA], StageBM<C>& D) {
 #pragma unroll
@@ -535,10 +632,8 @@ VIT_HD void fwd_stage(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], const Half (
 template <class C, int u>
 VIT_HD void fwd_stage_words(uint32_t (&mi)[C::NS], uint32_t (&mo)[C::NS], int i,
                             const uint32_t (&w)[2][C::U * C::BETA / 4], Slab sl) {
-  int L[C::BETA];
-  pairs_from_words<C, u>(w, L);
   StageBM<C> D;
-  bm_from_pairs<C>(L, D);
+  bm_from_words<C, u>(w, D);
   uint32_t wd[C::WORDS];
   acs_stage<C>(mi, mo, D, wd);
   store_words(sl.base + (int64_t)i * sl.stride, wd, C::WORDS);

@@ -3,6 +3,7 @@
 // tile decoder, de-puncturing and encoder kernels.
 #include <cuda_runtime.h>
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
