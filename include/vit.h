@@ -117,12 +117,18 @@ int vit_set_parallel_traceback(vit_code* code, int64_t f0, int rule, uint64_t se
  * tile with the decisions in shared memory (Sec. "Unified Kernel": the
  * survivors never leave the SM) for frames of at most 1024 tiles whose
  * windows fit 6144 stages, else the tile decoder (two tiles per lane, 64 per
- * warp, survivor words in the scratch slab).  VIT_DECODER_TILES always uses
- * the tile decoder; VIT_DECODER_SHARED always uses the shared-memory decoder
- * (any number of tiles; VIT_EUNSUPPORTED at decode time when a window exceeds
- * 6144 stages or the code has no such decoder: K > 7 with compiled kernels).
+ * warp, survivor words in the scratch slab), or -- when the frame has too
+ * few tiles to keep half of that decoder's resident warps busy and the code
+ * has one -- the spread tile decoder (each tile pair over four lanes, 16
+ * tiles per warp; compiled for the K=7 rate-1/2 codes (171,133) and
+ * (133,171)).  VIT_DECODER_TILES always uses the two-tiles-per-lane decoder,
+ * VIT_DECODER_SPREAD the spread one (VIT_EUNSUPPORTED at decode time for
+ * codes without it); VIT_DECODER_SHARED always uses the shared-memory
+ * decoder (any number of tiles; VIT_EUNSUPPORTED at decode time when a
+ * window exceeds 6144 stages or the code has no such decoder: K > 7 with
+ * compiled kernels).
  */
-enum { VIT_DECODER_AUTO = 0, VIT_DECODER_TILES = 1, VIT_DECODER_SHARED = 2 };
+enum { VIT_DECODER_AUTO = 0, VIT_DECODER_TILES = 1, VIT_DECODER_SHARED = 2, VIT_DECODER_SPREAD = 3 };
 int vit_set_decoder(vit_code* code, int which);
 
 void vit_destroy(vit_code* code);

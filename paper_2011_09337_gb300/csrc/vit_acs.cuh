@@ -53,11 +53,13 @@ VIT_CX uint32_t rotr_w(uint32_t x, int r, int w) {
 constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
 
 // A rate-1/beta code with constraint length K and generators G0..G3 (bit K-1
-// taps the current input, Eq. 1).
-template <int K_, int B_, uint32_t G0, uint32_t G1, uint32_t G2 = 0, uint32_t G3 = 0>
+// taps the current input, Eq. 1).  NSMAX caps the states one lane holds: a
+// smaller cap spreads each tile pair over more lanes (S / NSMAX), which
+// gives frames with few tiles more warps.
+template <int K_, int B_, uint32_t G0, uint32_t G1, uint32_t G2 = 0, uint32_t G3 = 0, int NSMAX = 64>
 struct Code {
   static constexpr int K = K_, BETA = B_, KM1 = K_ - 1, S = 1 << (K_ - 1);
-  static constexpr int NS = S < 64 ? S : 64;            // states (slots) per lane
+  static constexpr int NS = S < NSMAX ? S : NSMAX;      // states (slots) per lane
   static constexpr int G = S / NS;                      // lanes per tile pair
   static constexpr int NSB = ilog2c(NS);                // slot bits held in registers
   static constexpr int WORDS = NS >= 16 ? NS / 16 : 1;  // survivor words per lane per stage

@@ -182,6 +182,25 @@ void register_warp(const MixKey& k, LaunchFn launch) {
   warp_registry().push_back(PtReg{k, launch});
 }
 
+struct SpreadReg {
+  MixKey key;
+  const CodeEntry* entry;
+};
+std::vector<SpreadReg>& spread_registry() {
+  static std::vector<SpreadReg> r;
+  return r;
+}
+void register_spread(const MixKey& k, const CodeEntry* e) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  spread_registry().push_back(SpreadReg{k, e});
+}
+const CodeEntry* find_spread(const CodeEntry* e) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (const SpreadReg& r : spread_registry())
+    if (key_matches(r.key, e)) return r.entry;
+  return nullptr;
+}
+
 LaunchFn find_warp(const CodeEntry* e) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   for (const PtReg& r : warp_registry())
@@ -296,6 +315,7 @@ int vit_create(vit_code** out, int K, int beta, const uint32_t* polys, int64_t f
   c->mode = VIT_STREAM;
   c->entry = e;
   c->warp_launch = e->generic ? find_warp_generic(K, beta) : find_warp(e);
+  c->spread = e->generic ? nullptr : find_spread(e);
   *out = c;
   return VIT_OK;
 }
@@ -356,7 +376,8 @@ int vit_set_parallel_traceback(vit_code* c, int64_t f0, int rule, uint64_t seed)
 
 int vit_set_decoder(vit_code* c, int which) {
   if (int r = check_code(c)) return r;
-  if (which != VIT_DECODER_AUTO && which != VIT_DECODER_TILES && which != VIT_DECODER_SHARED)
+  if (which != VIT_DECODER_AUTO && which != VIT_DECODER_TILES && which != VIT_DECODER_SHARED &&
+      which != VIT_DECODER_SPREAD)
     return fail(VIT_EINVAL, "invalid decoder choice %d", which);
   c->decoder = which;
   return VIT_OK;
@@ -382,11 +403,25 @@ static int64_t pt_subframes(const vit_code* c, int64_t n) {
   return (fb + c->pt_f0 - 1) / c->pt_f0;
 }
 
-static size_t slab_task_words(const vit_code* c, int64_t n) {
+static size_t slab_task_words(const vit_code* c, const CodeEntry* e, int64_t n) {
   const int64_t L = max_window(c, n);
-  const int64_t U = c->entry->unroll;
+  const int64_t U = e->unroll;
   const int64_t Lr = (L + U - 1) / U * U;
-  return (size_t)Lr * c->entry->slab_lanes * c->entry->words;
+  return (size_t)Lr * e->slab_lanes * e->words;
+}
+
+static int64_t task_count(const CodeEntry* e, int64_t tiles) {
+  return (tiles + e->tiles_per_task - 1) / e->tiles_per_task;
+}
+
+// The tile decoder of a single-frame decode: the code's own, or (when the
+// frame's warp tasks would leave at least half of the decoder's resident
+// warps idle, or when asked) the variant with several lanes per tile pair.
+static const CodeEntry* tile_entry(const vit_code* c, int64_t n) {
+  if (c->spread == nullptr || c->pt_f0 > 0 || c->decoder == VIT_DECODER_TILES) return c->entry;
+  if (c->decoder == VIT_DECODER_SPREAD) return c->spread;
+  const int64_t r = c->entry->resident ? c->entry->resident(kWarpsPerCta) : 0;
+  return (r > 0 && 2 * task_count(c->entry, tile_count(n, c->f)) <= r) ? c->spread : c->entry;
 }
 
 // Slab slots of a single-frame decode with the tile decoder: 0 (one per
@@ -394,19 +429,19 @@ static size_t slab_task_words(const vit_code* c, int64_t n) {
 // number of warps resident on the current device, which then stride over the
 // tasks and reuse their slots -- the slab stops growing with n after one
 // wave.  The parallel-traceback decoder keeps one slot per task.
-static int64_t slab_slots(const vit_code* c, int64_t tasks) {
-  if (c->pt_f0 > 0 || c->entry->resident == nullptr) return 0;
-  const int64_t r = c->entry->resident(kWarpsPerCta);
+static int64_t slab_slots(const vit_code* c, const CodeEntry* e, int64_t tasks) {
+  if (c->pt_f0 > 0 || e->resident == nullptr) return 0;
+  const int64_t r = e->resident(kWarpsPerCta);
   return (r > 0 && tasks > r) ? r : 0;
 }
 
 size_t vit_decode_workspace(const vit_code* c, int64_t n) {
   if (c == nullptr || n <= 0) return 0;
   const int64_t tiles = tile_count(n, c->f);
-  const int64_t tpt = c->entry->tiles_per_task;
-  const int64_t tasks = (tiles + tpt - 1) / tpt;
-  const int64_t slots = slab_slots(c, tasks);
-  size_t bytes = align_up((size_t)(slots ? slots : tasks) * slab_task_words(c, n) * 4);
+  const CodeEntry* e = tile_entry(c, n);
+  const int64_t tasks = task_count(e, tiles);
+  const int64_t slots = slab_slots(c, e, tasks);
+  size_t bytes = align_up((size_t)(slots ? slots : tasks) * slab_task_words(c, e, n) * 4);
   if (c->period) bytes += align_up((size_t)n * c->beta);
   bytes += align_up((size_t)(tiles * pt_subframes(c, n)));
   return bytes;
@@ -415,10 +450,10 @@ size_t vit_decode_workspace(const vit_code* c, int64_t n) {
 static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t* bits_out, void* ws,
                        size_t ws_bytes, cudaStream_t s) {
   const int64_t tiles = tile_count(n, c->f);
-  const int64_t tpt = c->entry->tiles_per_task;
-  const int64_t tasks = (tiles + tpt - 1) / tpt;
-  const size_t tw = slab_task_words(c, n);
-  const int64_t slots = slab_slots(c, tasks);
+  const CodeEntry* te = tile_entry(c, n);
+  const int64_t tasks = task_count(te, tiles);
+  const size_t tw = slab_task_words(c, te, n);
+  const int64_t slots = slab_slots(c, te, tasks);
   uint8_t* p = (uint8_t*)ws;
   uint32_t* slab = (uint32_t*)p;
   p += align_up((size_t)(slots ? slots : tasks) * tw * 4);
@@ -470,10 +505,12 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
     a.pt_nsub = pt_subframes(c, n);
     a.pt_states = p;
   }
-  LaunchFn launch = c->pt_f0 > 0 ? c->pt_launch : c->entry->launch;
+  LaunchFn launch = c->pt_f0 > 0 ? c->pt_launch : te->launch;
   // few short tiles: one warp per tile decodes them with lower latency
   const bool fits = c->warp_launch != nullptr && max_window(c, n) <= kWarpSmemStages;
   if (c->pt_f0 == 0 && c->decoder == VIT_DECODER_AUTO && fits && tiles <= kWarpTileLimit) launch = c->warp_launch;
+  if (c->decoder == VIT_DECODER_SPREAD && c->spread == nullptr)
+    return fail(VIT_EUNSUPPORTED, "no tile decoder with several lanes per tile pair for this code");
   if (c->decoder == VIT_DECODER_SHARED) {
     if (!fits || c->pt_f0 > 0)
       return fail(VIT_EUNSUPPORTED, "the shared-memory decoder needs windows of at most %d stages, no parallel "

@@ -317,6 +317,11 @@ void register_generic(const CodeEntry* e);
 const CodeEntry* find_generic(int K, int beta);
 void register_warp_generic(int K, int beta, LaunchFn launch);
 LaunchFn find_warp_generic(int K, int beta);
+// Tile decoders that spread each tile pair over several lanes (fewer tiles
+// per warp task), for frames with too few tiles to fill the GPU, by
+// (K, beta, polys).
+void register_spread(const MixKey& k, const CodeEntry* e);
+const CodeEntry* find_spread(const CodeEntry* e);
 
 }  // namespace vit
 
@@ -334,7 +339,8 @@ struct vit_code {
   uint64_t pt_seed;
   vit::LaunchFn pt_launch;
   vit::LaunchFn warp_launch;  // warp-per-tile decoder, or nullptr
-  int decoder;                // VIT_DECODER_AUTO, _TILES or _SHARED
+  const vit::CodeEntry* spread;  // tile decoder with several lanes per tile pair, or nullptr
+  int decoder;                // VIT_DECODER_AUTO, _TILES, _SHARED or _SPREAD
 };
 
 namespace vit {

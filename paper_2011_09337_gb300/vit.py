@@ -16,7 +16,7 @@ import torch
 from . import build_lib
 
 STREAM, TERMINATED, FREE_START = 0, 1, 2
-DECODER_AUTO, DECODER_TILES, DECODER_SHARED = 0, 1, 2
+DECODER_AUTO, DECODER_TILES, DECODER_SHARED, DECODER_SPREAD = 0, 1, 2, 3
 BATCH_GRAPH, BATCH_PERSISTENT, BATCH_HOST = 1, 4, 8
 PT_STORED, PT_RANDOM = 0, 1
 
@@ -106,7 +106,8 @@ class Code:
                  pt_seed: int = 0, decoder: int = DECODER_AUTO):
         """pt_f0 > 0 selects the parallel traceback with subframes of pt_f0
         stages (pt_rule: PT_STORED or PT_RANDOM, pt_seed: SplitMix64 key);
-        decoder: DECODER_AUTO, DECODER_TILES or DECODER_SHARED (vit_set_decoder)."""
+        decoder: DECODER_AUTO, DECODER_TILES, DECODER_SHARED or DECODER_SPREAD
+        (vit_set_decoder)."""
         L = load()
         self.K, self.beta, self.polys = K, beta, tuple(int(p) for p in polys)
         self.f = f

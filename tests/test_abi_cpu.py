@@ -94,9 +94,9 @@ def test_decoder_choice_is_validated(lib):
     lib.vit_set_decoder.argtypes = [ctypes.c_void_p, ctypes.c_int]
     rc, h = _create(lib, 7, 2, (0o171, 0o133), 1024, 48)
     assert rc == 0
-    for which in (0, 1, 2):
+    for which in (0, 1, 2, 3):
         assert lib.vit_set_decoder(h, which) == 0
-    assert lib.vit_set_decoder(h, 3) == -1
+    assert lib.vit_set_decoder(h, 4) == -1
     assert lib.vit_set_decoder(None, 0) == -1
     lib.vit_destroy(h)
 

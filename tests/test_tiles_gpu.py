@@ -3,12 +3,14 @@ compiled code.
 
 Single frames of at most 1024 tiles go to the warp-per-tile decoder, so the
 frames here are cut into more than 1024 tiles (f = 8 or 16): every case
-below runs the tile decoder (Alg. 1 + Alg. 2 on the overlapped tiles of Fig.
+below runs a tile decoder (Alg. 1 + Alg. 2 on the overlapped tiles of Fig.
 relworks), including warp tasks whose last tiles are missing, a short last
 tile, windows clipped at both frame ends, asymmetric overlaps, saturated and
 all-zero LLRs, and an LLR buffer that starts at an odd address (byte loads
-instead of the 32-bit word loads).  Decoded bits are compared with
-``oracle.viterbi_blocked`` element by element.
+instead of the 32-bit word loads).  The K=7 rate-1/2 codes run both their
+two-tiles-per-lane decoder and their spread decoder (four lanes per tile
+pair).  Decoded bits are compared with ``oracle.viterbi_blocked`` element by
+element.
 """
 import numpy as np
 import pytest
@@ -46,11 +48,19 @@ def _enc(code):
     return lambda x: oracle.encode(K, beta, polys, x)
 
 
-def _decode(vit, key, llr, n, f, v1, v2, mode, offset=0):
+SPREAD = ("k7", "k7swap")  # codes with a compiled spread tile decoder
+
+
+def _decoders(vit, key):
+    return [vit.DECODER_TILES] + ([vit.DECODER_SPREAD] if key in SPREAD else [])
+
+
+def _decode(vit, key, llr, n, f, v1, v2, mode, offset=0, decoder=None):
     """Decodes through vit_decode_ws; ``offset`` places the LLRs that many
     bytes into a larger device buffer."""
     K, beta, polys = CODES[key]
-    c = vit.Code(K, beta, polys, f=f, v=v1, v1=v1, v2=v2, mode=mode)
+    c = vit.Code(K, beta, polys, f=f, v=v1, v1=v1, v2=v2, mode=mode,
+                 decoder=vit.DECODER_TILES if decoder is None else decoder)
     flat = np.ascontiguousarray(llr).reshape(-1)
     buf = torch.zeros(flat.size + 16, dtype=torch.int8, device="cuda")
     buf[offset:offset + flat.size] = torch.from_numpy(flat).cuda()
@@ -74,8 +84,10 @@ def test_tile_decoder_matches_oracle(vit, key, mode):
         assert (n + f - 1) // f > 1024
         s = synth.make_stream(_enc(CODES[key]), beta, n, 1.0 + i, seed=1000 * i + 10 * mode + K, tail=tail)
         want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v1, v2, mode)[: n - tail]
-        got = _decode(vit, key, s.llr, n, f, v1, v2, mode)
-        np.testing.assert_array_equal(got, want, err_msg=f"{key} mode={mode} n={n} f={f} v1={v1} v2={v2}")
+        for d in _decoders(vit, key):
+            got = _decode(vit, key, s.llr, n, f, v1, v2, mode, decoder=d)
+            np.testing.assert_array_equal(got, want,
+                                          err_msg=f"{key} mode={mode} n={n} f={f} v1={v1} v2={v2} decoder={d}")
 
 
 @pytest.mark.parametrize("key", list(CODES))
@@ -90,11 +102,12 @@ def test_tile_decoder_extreme_llrs(vit, key):
             g.integers(-1, 2, size=(n, beta)).astype(np.int8)]
     for j, llr in enumerate(llrs):
         want = oracle.viterbi_blocked(K, beta, polys, llr, f, v, v)
-        got = _decode(vit, key, llr, n, f, v, v, oracle.STREAM)
-        np.testing.assert_array_equal(got, want, err_msg=f"{key} llr set {j}")
+        for d in _decoders(vit, key):
+            got = _decode(vit, key, llr, n, f, v, v, oracle.STREAM, decoder=d)
+            np.testing.assert_array_equal(got, want, err_msg=f"{key} llr set {j} decoder={d}")
 
 
-@pytest.mark.parametrize("key", ["k7", "k7r13", "k9", "k4b4"])
+@pytest.mark.parametrize("key", ["k7", "k7swap", "k7r13", "k9", "k4b4"])
 @pytest.mark.parametrize("offset", [1, 2, 3])
 def test_tile_decoder_unaligned_llrs(vit, key, offset):
     """LLRs at an address that is not a multiple of 4: the warp tasks cannot
@@ -103,8 +116,9 @@ def test_tile_decoder_unaligned_llrs(vit, key, offset):
     n, f, v = 16 * 1030 + 11, 16, 3 * (K - 1)
     s = synth.make_stream(_enc(CODES[key]), beta, n, 2.5, seed=offset + 7 * K)
     want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v)
-    got = _decode(vit, key, s.llr, n, f, v, v, oracle.STREAM, offset=offset)
-    np.testing.assert_array_equal(got, want)
+    for d in _decoders(vit, key):
+        got = _decode(vit, key, s.llr, n, f, v, v, oracle.STREAM, offset=offset, decoder=d)
+        np.testing.assert_array_equal(got, want, err_msg=f"decoder={d}")
 
 
 @pytest.mark.parametrize("key", ["k7", "k7r13", "k5", "k6asym"])
@@ -125,6 +139,31 @@ def test_decoder_choice(vit, key):
     x = torch.zeros(7000 * beta, dtype=torch.int8, device="cuda")
     with pytest.raises(vit.VitError):
         vit.decode(c, x, n=7000)
+    if key not in SPREAD:  # no spread decoder compiled
+        c = vit.Code(K, beta, polys, f=64, v=20, decoder=vit.DECODER_SPREAD)
+        with pytest.raises(vit.VitError):
+            vit.decode(c, x, n=7000)
+
+
+def test_auto_picks_the_spread_decoder_for_few_tiles(vit):
+    """A 2^21-stage K=7 stream at f=1024 has 32 warp tasks of 64 tiles; the
+    automatic choice gives it the spread decoder (128 tasks of 16 tiles) and
+    the bits match the oracle on sampled tiles; workspace follows the
+    choice (the spread slab rounds windows to 6 stages instead of 2)."""
+    K, beta, polys = CODES["k7"]
+    n = 1 << 21
+    s = synth.make_stream(_enc(CODES["k7"]), beta, n, 1.0, seed=21)
+    x = torch.from_numpy(s.llr.reshape(-1)).cuda()
+    outs = {}
+    for d in (vit.DECODER_AUTO, vit.DECODER_TILES, vit.DECODER_SPREAD):
+        c = vit.Code(K, beta, polys, f=1024, v=48, decoder=d)
+        outs[d] = (synth.unpack_bits(vit.decode(c, x, n=n).cpu().numpy(), n), c.workspace_bytes(n))
+    assert outs[vit.DECODER_AUTO][1] == outs[vit.DECODER_SPREAD][1] != outs[vit.DECODER_TILES][1]
+    np.testing.assert_array_equal(outs[vit.DECODER_AUTO][0], outs[vit.DECODER_TILES][0])
+    np.testing.assert_array_equal(outs[vit.DECODER_SPREAD][0], outs[vit.DECODER_TILES][0])
+    for b in (0, 1, 777, 2047):
+        want = oracle.viterbi_blocked(K, beta, polys, s.llr, 1024, 48, 48, blocks=(b, b + 1))
+        np.testing.assert_array_equal(outs[vit.DECODER_AUTO][0][b * 1024:(b + 1) * 1024], want[b * 1024:(b + 1) * 1024])
 
 
 @pytest.mark.parametrize("key", ["k7", "k9"])
