@@ -415,13 +415,16 @@ static int64_t task_count(const CodeEntry* e, int64_t tiles) {
 }
 
 // The tile decoder of a single-frame decode: the code's own, or (when the
-// frame's warp tasks would leave at least half of the decoder's resident
-// warps idle, or when asked) the variant with several lanes per tile pair.
+// frame's warp tasks would fill at most a quarter of the decoder's resident
+// warps, or when asked) the variant with several lanes per tile pair.  Timed
+// on a GB300: a 2^24-bit K=7 stream at f=1024 (256 tasks, 14% of the
+// resident warps) decodes 1.4x faster spread; a 2^26-bit stream at f=2048
+// (512 tasks, 28%) 5-10% slower, so the cut is at a quarter.
 static const CodeEntry* tile_entry(const vit_code* c, int64_t n) {
   if (c->spread == nullptr || c->pt_f0 > 0 || c->decoder == VIT_DECODER_TILES) return c->entry;
   if (c->decoder == VIT_DECODER_SPREAD) return c->spread;
   const int64_t r = c->entry->resident ? c->entry->resident(kWarpsPerCta) : 0;
-  return (r > 0 && 2 * task_count(c->entry, tile_count(n, c->f)) <= r) ? c->spread : c->entry;
+  return (r > 0 && 4 * task_count(c->entry, tile_count(n, c->f)) <= r) ? c->spread : c->entry;
 }
 
 // Slab slots of a single-frame decode with the tile decoder: 0 (one per
