@@ -154,6 +154,10 @@ __global__ void __maxnreg__((C::G > 1 && kWords) ? kMaxRegsRotWords : kMaxRegs) 
 
 // Persistent kernel over the tasks of two codes: each warp takes the next
 // entry of a cost-ordered queue (one atomic per task) until it is empty.
+// Both task bodies are inlined, so the kernel runs with the larger register
+// allocation of the two (out-of-line bodies kept them apart but paid for the
+// calls in spills: 0.98 against 0.90 ms on the mixed benchmark batch; the
+// same plan as two concurrent launches takes 0.54 ms and is the default).
 struct MixTask {
   int32_t code;  // 0 or 1
   int32_t pad;
@@ -166,12 +170,6 @@ struct MixArgs {
   unsigned long long* counter;  // zeroed before every launch
 };
 
-// Out-of-line task bodies keep the two codes' register allocations apart.
-template <class C>
-__device__ __noinline__ void run_task_call(const KArgs a, int64_t task, int lane) {
-  run_task<C, (C::G == 1)>(a, task, task, lane);
-}
-
 template <class C0, class C1>
 __global__ void __maxnreg__(kMaxRegs) decode_mixed_kernel(const MixArgs a) {
   const int lane = threadIdx.x & 31;
@@ -182,9 +180,9 @@ __global__ void __maxnreg__(kMaxRegs) decode_mixed_kernel(const MixArgs a) {
     if (q >= (unsigned long long)a.nqueue) break;
     const MixTask t = a.queue[q];
     if (t.code == 0)
-      run_task_call<C0>(a.g[0], t.task, lane);
+      run_task<C0, (C0::G == 1)>(a.g[0], t.task, t.task, lane);
     else
-      run_task_call<C1>(a.g[1], t.task, lane);
+      run_task<C1, (C1::G == 1)>(a.g[1], t.task, t.task, lane);
   }
 }
 #endif
