@@ -73,13 +73,16 @@ def fp_peak_leg(vit, device):
     return out
 
 
+# the sources of the timed kernel (the K=7 tile decoder and its launcher)
+HOT_SOURCES = ("vit_acs.cuh", "vit_internal.h", "vit_codes_k7.cu")
+
+
 def _kernel_source_sha() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2011_09337_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+    for name in HOT_SOURCES:
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -678,9 +681,11 @@ def main():
                     help="build the workload with --streams streams, run the planned batch twice and exit "
                          "(the target of the ncu captures)")
     ap.add_argument("--streams", type=int, default=len(EBN0))
-    ap.add_argument("--profile-code", default="k7", choices=["k7", "k9", "frame"],
+    ap.add_argument("--profile-code", default="k7", choices=["k7", "k9", "frame", "probe", "metric"],
                     help="with --profile: k7 = the batch above; k9 = one 2^25-bit K=9 (561,753) stream, "
-                         "f=2048, v=96, decoded twice; frame = the single-frame latency case, decoded twice")
+                         "f=2048, v=96, decoded twice; frame = the single-frame latency case, decoded twice; "
+                         "probe = the instruction-rate probes of the roofline peak, once each; metric = the "
+                         "path-metric workload, forward and backward once per form")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -701,6 +706,15 @@ def main():
     from paper_2011_09337_gb300 import vit
     if args.profile and args.profile_code == "k9":
         profile_k9(vit, torch, dev)
+        return
+    if args.profile and args.profile_code == "probe":
+        print(json.dumps({"profile_run": "ok", "code": "probe", "int": alu_peak_leg(vit, dev),
+                          "fp": fp_peak_leg(vit, dev)}))
+        return
+    if args.profile and args.profile_code == "metric":
+        m = metric_leg(vit, torch, dev, 1, fp_peak_leg(vit, dev), _peaks()[0])
+        print(json.dumps({"profile_run": "ok", "code": "metric",
+                          **{k: m[k] for k in ("hard", "tau_0.5", "tau_1", "tau_2")}}))
         return
     if args.profile and args.profile_code == "frame":
         print(json.dumps({"profile_run": "ok", "code": "frame", **frame_latency_leg(vit, torch, dev, 2)}))

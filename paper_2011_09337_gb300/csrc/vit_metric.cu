@@ -215,11 +215,20 @@ __global__ void __launch_bounds__(kWarps * 32) metric_bwd_hard_kernel(const MArg
   const float g = a.gmet[f];
   float* grad = a.grad + (int64_t)f * a.n * a.beta;
   uint32_t J = 0;  // state after the last stage (terminated)
+  uint32_t wn[R];   // the next (lower) block's words, loaded one block ahead
+  {
+    const int64_t my = ((a.n - 1) / 32) * 32 + lane;
+#pragma unroll
+    for (int r = 0; r < R; r++) wn[r] = (my < a.n) ? dw[my * R + r] : 0u;
+  }
   for (int64_t b0 = ((a.n - 1) / 32) * 32; b0 >= 0; b0 -= 32) {
     const int64_t my = b0 + lane;
     uint32_t wv[R];
 #pragma unroll
-    for (int r = 0; r < R; r++) wv[r] = (my < a.n) ? dw[my * R + r] : 0u;
+    for (int r = 0; r < R; r++) {
+      wv[r] = wn[r];
+      wn[r] = (b0 >= 32) ? dw[(b0 - 32 + lane) * R + r] : 0u;
+    }
     const int top = (a.n - b0 < 32) ? (int)(a.n - b0) : 32;
     uint32_t myR = 0;
     for (int k = top - 1; k >= 0; k--) {
