@@ -573,14 +573,18 @@ def metric_leg(vit, torch, device, steps, fp_rates, sm_mhz):
                                  "frac": ach / peak, "ops": "4 FP32 ops per state per stage"}
         else:
             # one exp and one log per state per stage in the forward pass; the
-            # backward recomputes the forward (2), runs the beta recursion (2)
-            # and forms two branch posteriors (2 exp)
-            peak = min(fp_rates["ex2"], fp_rates["lg2"]) * 32 * sms * sm_mhz * 1e6
-            for leg, mufu, ms in (("fwd", 2.0, fwd_ms), ("bwd", 6.0, bwd_ms)):
+            # backward recomputes the forward (exp, log), runs the beta
+            # recursion (exp, log) and forms two branch posteriors (2 exp).
+            # The peak of each mix: its MUFU instructions over the cycles they
+            # occupy at the measured ex2 and lg2 rates.
+            for leg, nex, nlg, ms in (("fwd", 1.0, 1.0, fwd_ms), ("bwd", 4.0, 2.0, bwd_ms)):
+                mufu = nex + nlg
+                rate = mufu / (nex / fp_rates["ex2"] + nlg / fp_rates["lg2"])
+                peak = rate * 32 * sms * sm_mhz * 1e6
                 ach = mufu * state_stages / (ms * 1e-3)
                 r[f"roofline_{leg}"] = {"bound": "mufu", "achieved": ach / 1e12, "peak": peak / 1e12,
                                         "unit": "Tops/s", "frac": ach / peak,
-                                        "ops": f"{mufu:g} MUFU ops per state per stage"}
+                                        "ops": f"{nex:g} ex2 + {nlg:g} lg2 per state per stage"}
         out[key] = r
         del xr, m, gx
     return out

@@ -312,7 +312,11 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
       }
     }
     __syncwarp();
-    // beta recursion and posteriors, 32 stages at a time from the top
+    // beta recursion and posteriors, 32 stages at a time from the top; the
+    // lane's alphas of the stage below are loaded one stage ahead
+    float aln[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) aln[r] = live ? seg[(t1 - 1 - t0) * S + R * lane + r] : -INFINITY;
     for (int64_t hi = t1; hi > t0; hi -= 32) {
       const int64_t lo = (hi - 32 > t0) ? hi - 32 : t0;
       float lv[4];
@@ -321,13 +325,19 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
         const int k = (int)(t - lo);
         float l[4];
         stage_llr(lv, k, l);
+        float al[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          al[r] = aln[r];
+          aln[r] = (live && t - 1 >= t0) ? seg[(t - 1 - t0) * S + R * lane + r] : -INFINITY;
+        }
         float v0[R], v1[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
           v0[r] = __shfl_sync(0xffffffffu, bt[r], src0);
           v1[r] = __shfl_sync(0xffffffffu, bt[r], src1);
         }
-        float u0[R], u1[R], al[R];
+        float u0[R], u1[R];
         float mx = -INFINITY;
 #pragma unroll
         for (int r = 0; r < R; r++) {
@@ -344,7 +354,6 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
           }
           u0[r] = bm4(s0[r], l) + bj0;
           u1[r] = bm4(s1[r], l) + bj1;
-          al[r] = live ? seg[(t - t0) * S + R * lane + r] : -INFINITY;
           if (live) mx = fmaxf(mx, fmaxf(al[r] + u0[r], al[r] + u1[r]));
         }
 #pragma unroll
