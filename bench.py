@@ -515,7 +515,31 @@ def mixed_batch_leg(vit, torch, device, steps):
         "tuned": {str(ci): {"f": chosen[ci].f, "v": chosen[ci].v, "disagree_vs_full_frame": chosen[ci].disagree}
                   for ci in chosen} | {"warps_per_cta": warps},
         "ber": err / info_bits, "info_bits": info_bits,
+        "alu": _mixed_alu(frames, codes, chosen, ms_batch, ms_persistent),
     }
+
+
+def _window_stages(n: int, f: int, v: int) -> int:
+    """Stages processed by the tiles of an n-stage frame (windows clipped to
+    the frame; f = 0 is one window)."""
+    fb = n if (f == 0 or f > n) else f
+    tot = 0
+    for b in range((n + fb - 1) // fb):
+        e0, e1 = b * fb, min((b + 1) * fb, n)
+        tot += min(n, e1 + v) - max(0, e0 - v)
+    return tot
+
+
+def _mixed_alu(frames, codes, chosen, ms_batch, ms_persistent):
+    """Algorithmic int16 ops of the mixed batch (4 per state per processed
+    stage, overlaps included) over each launch form's step time, against the
+    measured peak."""
+    ops = 0.0
+    for ci, _, n, _ in frames:
+        K = codes[ci][0]
+        ops += 4.0 * (1 << (K - 1)) * _window_stages(n, chosen[ci].f, chosen[ci].v)
+    return {"ops_per_step": ops, "tops_concurrent": ops / (ms_batch * 1e-3) / 1e12,
+            "tops_persistent": ops / (ms_persistent * 1e-3) / 1e12}
 
 
 METRIC_WORKLOAD = ("1024 zero-terminated frames x (2048 + 6) stages, K=7 r1/2 (171,133), FP32 LLRs "
@@ -879,6 +903,13 @@ def main():
         "metric_leg": metric,
         "ber": {"vs_transmitted": ber_per_ebn0, "bits_per_stream": NBITS},
     }
+    if mixed is not None:
+        mixed["alu"]["frac_concurrent"] = mixed["alu"]["tops_concurrent"] / peak_tops
+        mixed["alu"]["frac_persistent"] = mixed["alu"]["tops_persistent"] / peak_tops
+    if large is not None:
+        for k, v in large.items():
+            if isinstance(v, dict) and "alu_tops" in v:
+                v["alu_frac"] = v["alu_tops"] / peak_tops
     if clocks.get("sm_mhz"):
         line["roofline"]["peak_at_sampled_clock"] = peak_tops * clocks["sm_mhz"] / sm_max
         line["roofline"]["frac_at_sampled_clock"] = achieved_tops / (peak_tops * clocks["sm_mhz"] / sm_max)
