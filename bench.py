@@ -260,6 +260,40 @@ def cpu_oracle_rate(seconds: float = 12.0):
             F / per_tile / 1e6)
 
 
+def other_configs_cpu_rate():
+    """One host thread of the oracle's tiled decoder on samples of the other
+    workloads: 8 tiles of the 2^26-bit K=9 stream (f=2048, v=96), 8 tiles of
+    the K=7 rate-3/4 stream (f=2048, v=64, de-punctured), and 64 frames of the
+    mixed batch's lengths at its tuned tilings (f=256, v=42 / 80)."""
+    import oracle
+    from paper_2011_09337_gb300 import synth
+    out = {}
+    for name, (k, b, p), f, v, mask in (("k9_stream", synth.CODE_K9_R12, 2048, 96, None),
+                                       ("k7_r34_stream", synth.CODE_K7_R12, 2048, 64, synth.PUNCT_R34)):
+        n = 10 * f
+        st = synth.make_stream(lambda x: oracle.encode(k, b, p, x), b, n, 4.0, seed=11, mask=mask)
+        llr = st.llr if mask is None else oracle.depuncture(st.llr, n, b, mask)
+        t0 = time.perf_counter()
+        oracle.viterbi_blocked(k, b, p, llr, f, v, v, blocks=(1, 9))
+        dt = time.perf_counter() - t0
+        out[name] = {"value": 8 * f / dt / 1e6, "unit": "Mbit/s", "cores": 1, "sample": f"8 tiles of {f} bits"}
+    spec = synth.mixed_batch_spec(64, 2)
+    codes = [synth.CODE_K7_R13, synth.CODE_K9_R12]
+    fv = [(256, 42), (256, 80)]
+    bits, dt = 0, 0.0
+    for fs in spec:
+        k, b, p = codes[fs.code]
+        n = fs.n_info + k - 1
+        st = synth.make_stream(lambda x: oracle.encode(k, b, p, x), b, n, fs.ebn0_db, seed=fs.seed, tail=k - 1)
+        t0 = time.perf_counter()
+        oracle.viterbi_blocked(k, b, p, st.llr, fv[fs.code][0], fv[fs.code][1], fv[fs.code][1], oracle.TERMINATED)
+        dt += time.perf_counter() - t0
+        bits += fs.n_info
+    out["mixed_batch"] = {"value": bits / dt / 1e6, "unit": "Mbit/s", "cores": 1,
+                          "sample": "64 frames of the mixed batch's length and code mix"}
+    return out
+
+
 def full_frame_oracle_sample(streams, got_bits, prefix=1 << 17, margin=1024):
     """The oracle's full-frame decoder (Alg. 1 + 2 over the whole prefix, one
     thread) on the first `prefix` stages of every stream: its rate, its BER
@@ -920,6 +954,7 @@ def main():
         if metric is not None:
             metric["cpu_baseline"] = metric_cpu_baseline()
         line["cpu_baseline"]["full_frame"] = full_frame_oracle_sample(streams, got_bits)
+        line["cpu_baseline"]["other_workloads_single_core"] = other_configs_cpu_rate()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
