@@ -864,9 +864,52 @@ def main():
         barrier()
         return a.elapsed_time(b) / steps
 
-    e2e_ms = timed(hbatch.run, args.steps)
-    e2e_value = bits_per_step * world / (e2e_ms * 1e-3) / 1e6
+    single_ms = timed(hbatch.run, args.steps)
     e2e_ok = all(torch.equal(h_out[i], d_out[i].cpu()) for i in range(len(streams)))
+
+    # double-buffered receiver: a second host-staged plan over its own pinned
+    # input and output buffers; consecutive steps alternate between the two
+    # plans on two streams, so one step's input copies overlap the previous
+    # step's decode.  Every step still copies its 235 MB in and its bits out.
+    h_llr2 = [torch.from_numpy(s.llr.reshape(-1)).pin_memory() for s in streams]
+    h_out2 = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in streams]
+    hbatch2 = vit.Batch([(code, h_llr2[i], NBITS, vit.STREAM, h_out2[i]) for i in range(len(streams))],
+                        graph=True, host=True, device=dev)
+    side = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    plans = [hbatch, hbatch2]
+    state = {"i": 0}
+
+    def pipelined_step():
+        k = state["i"] & 1
+        state["i"] += 1
+        side[k].wait_stream(stream)
+        with torch.cuda.stream(side[k]):
+            plans[k].run()
+        stream.wait_stream(side[k])
+
+    def pipelined(steps):
+        # the caller's stream forks each step to its plan's stream and joins it
+        # back only at the end, so steps on the two streams overlap
+        ev0 = torch.cuda.Event()
+        ev0.record(stream)
+        for k in range(steps):
+            j = k & 1
+            side[j].wait_event(ev0)
+            with torch.cuda.stream(side[j]):
+                plans[j].run()
+        stream.wait_stream(side[0])
+        stream.wait_stream(side[1])
+
+    for _ in range(max(2, args.warmup)):
+        pipelined_step()
+    barrier()
+    a.record(stream)
+    pipelined(args.steps)
+    b.record(stream)
+    barrier()
+    e2e_ms = a.elapsed_time(b) / args.steps
+    e2e_value = bits_per_step * world / (e2e_ms * 1e-3) / 1e6
+    e2e_ok = e2e_ok and all(torch.equal(h_out2[i], d_out[i].cpu()) for i in range(len(streams)))
 
     # the same copies and decode issued one after another on one stream
     def seq_step():
@@ -914,7 +957,10 @@ def main():
         "per_frame": {"value": per_frame_value, "unit": "Mbit/s", "launches_per_step": len(streams)},
         "e2e": {"value": e2e_value, "unit": "Mbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms, "api": "vit_batch_plan(VIT_BATCH_HOST) + vit_batch_run, pinned host buffers, "
-                "8 chunks (copies overlapped with decoding)", "matches_device_batch": e2e_ok,
+                "8 chunks (copies overlapped with decoding); two plans over two pinned buffer sets run on two "
+                "streams in turn, so consecutive steps overlap", "matches_device_batch": e2e_ok,
+                "single_plan": {"value": bits_per_step * world / (single_ms * 1e-3) / 1e6, "unit": "Mbit/s",
+                                "ms_per_step": single_ms, "how": "one host-staged plan, steps one after another"},
                 "sequential": {"value": bits_per_step * world / (seq_ms * 1e-3) / 1e6, "unit": "Mbit/s",
                                "ms_per_step": seq_ms, "how": "H2D, decode, D2H in turn on one stream"}},
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
