@@ -817,6 +817,7 @@ VIT_HD void decode_pair(const Half (&hw)[2], int Lw, int masked_until, uint32_t 
       constexpr int NW = C::U * C::BETA / 4;
       uint32_t wc[2][NW], wn[2][NW];
       if (g < ngroups) load_group_words<C>(hw, g * C::U, wc);
+#pragma unroll 2
       for (; g < ngroups; g++) {
         const int i0 = g * C::U;
         if (g + 1 < ngroups) load_group_words<C>(hw, i0 + C::U, wn);  // prefetch the next group
