@@ -11,15 +11,31 @@
 // the metrics of states R l + r (R = S / 32 for S >= 32, else one state per
 // lane l < S), the two predecessors of a state come from lanes 2l and 2l + 1
 // (mod 32) by shuffle, and each lane forms its branch patterns (Eq. 1) once.
-// The LLRs of 32 stages arrive with one coalesced load (lane k holds stage
-// i0 + k) and reach each stage by shuffle.  Every 32 stages the metrics are
-// re-referenced to state 0's (the offsets summed in fp64), so fp32 keeps
-// its precision over long frames.  Hard decisions are ballots (bit l of word
-// r = state R l + r), stored per block of 32 stages.  The soft backward
-// checkpoints alpha every C stages, recomputes a segment's alphas from its
-// checkpoint, and runs the beta recursion with lanes holding predecessor
-// states; the per-stage gradient sums go through shared memory, one stage per
-// lane, 32 stages at a time.
+// Every kernel is compiled per (R, beta), so branch metrics, LLR shuffles and
+// gradient sums carry exactly beta terms, and the 32 stages of a block are
+// unrolled.  The LLRs of 32 stages arrive with one coalesced load (lane k
+// holds stage i0 + k) and reach each stage by shuffle.  Every 32 stages the
+// metrics are re-referenced to state 0's (the offsets summed in fp64), so
+// fp32 keeps its precision over long frames.  Hard decisions are ballots
+// (bit l of word r = state R l + r), stored per block of 32 stages.  The soft
+// backward checkpoints alpha every C stages, recomputes a segment's alphas
+// from its checkpoint, and runs the beta recursion with lanes holding
+// predecessor states; the per-stage gradient sums go through shared memory,
+// one stage per lane, 32 stages at a time.
+//
+// Log-sum-exp in base 2: tau log(e^{x/tau} + e^{y/tau}) = max(x, y) +
+// tau ln2 log2(1 + 2^{-|x - y| log2(e) / tau}), with the hardware base-2
+// approximations (ex2, lg2) and no branch.
+//
+// Posterior reference.  Every path crosses exactly one branch of a stage, so
+// the branch totals x = alpha_t(i) + delta_t(i, j) + beta_{t+1}(j) of a stage
+// satisfy sum_branches exp(x / tau) = exp(M_tau / tau): the largest x lies in
+// [M_tau - tau ln(2S), M_tau] at every stage.  The backward therefore scales a
+// stage's posteriors by exp(-M_tau / tau) (less the offsets that re-reference
+// alpha and beta), which needs no reduction over the warp; the forward keeps
+// M_tau and its offset at each checkpoint in the workspace for that.  The
+// gradient is a ratio of two sums with the same scale, so the reference
+// changes no result beyond rounding.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -32,6 +48,8 @@ namespace {
 
 constexpr int kWarps = 4;      // frames per CTA (forward, hard backward)
 constexpr int kWarpsSoft = 2;  // frames per CTA of the soft backward (its shared reduction buffer)
+constexpr float kLog2e = 1.4426950408889634f;  // log2(e)
+constexpr float kLn2 = 0.6931471805599453f;    // ln(2)
 
 struct MArgs {
   int K, beta, S, spl;  // spl: states per lane (R)
@@ -49,6 +67,13 @@ struct MArgs {
   int64_t nck;          // checkpoints per frame (soft)
 };
 
+// Soft workspace of one frame: nck checkpoint rows and C segment rows of S
+// floats, then nck + 1 doubles: the forward's re-reference offset at each
+// checkpoint, and M_tau.
+__host__ __device__ inline size_t soft_offsets_at(int64_t nck, int C, int S) {
+  return (size_t)(nck + C) * (size_t)S * sizeof(float);
+}
+
 // output pattern of register word Rw (Eq. 1)
 __device__ __forceinline__ uint32_t aout_m(const MArgs& a, uint32_t Rw) {
   uint32_t o = 0;
@@ -58,30 +83,53 @@ __device__ __forceinline__ uint32_t aout_m(const MArgs& a, uint32_t Rw) {
   return o;
 }
 
-// signed branch metric sum_b (-1)^{c_b} l_b
-__device__ __forceinline__ float bm4(const float (&s)[4], const float (&l)[4]) {
-  return s[0] * l[0] + s[1] * l[1] + s[2] * l[2] + s[3] * l[3];
-}
-
-__device__ __forceinline__ void signs(const MArgs& a, uint32_t c, float (&s)[4]) {
+template <int B>
+__device__ __forceinline__ void signs(uint32_t c, float (&s)[B]) {
 #pragma unroll
-  for (int b = 0; b < 4; b++) s[b] = (b < a.beta) ? (((c >> b) & 1u) ? -1.f : 1.f) : 0.f;
+  for (int b = 0; b < B; b++) s[b] = ((c >> b) & 1u) ? -1.f : 1.f;
 }
 
-// tau log(exp(x/tau) + exp(y/tau)) = max + tau log(1 + e), e = exp(-|x-y|/tau)
-// in (0, 1]: both transcendentals are the hardware approximations (1 + e
-// lies in [1, 2], where the logarithm's absolute error is ~1e-7)
-__device__ __forceinline__ float lse2(float x, float y, float tau, float inv_tau) {
+// signed branch metric sum_b (-1)^{c_b} l_b
+template <int B>
+__device__ __forceinline__ float bmv(const float (&s)[B], const float (&l)[B]) {
+  float acc = s[0] * l[0];
+#pragma unroll
+  for (int b = 1; b < B; b++) acc = fmaf(s[b], l[b], acc);
+  return acc;
+}
+
+__device__ __forceinline__ float ex2a(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2a(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Base-2 constants of the log-sum-exp of temperature tau.
+struct Lse {
+  float k1;  // log2(e) / tau
+  float k2;  // tau ln 2
+  __device__ explicit Lse(float tau) : k1(kLog2e / tau), k2(tau * kLn2) {}
+};
+
+// tau log(exp(x/tau) + exp(y/tau)).  1 + e lies in [1, 2], where lg2's
+// absolute error is ~1e-7.  When both inputs are -inf, |x - y| is NaN and
+// fminf returns 1e30 instead, so e = 0 and the result is max = -inf.
+__device__ __forceinline__ float lse2(float x, float y, const Lse& c) {
   const float mx = fmaxf(x, y);
-  if (mx == -INFINITY) return -INFINITY;
-  return mx + tau * __logf(1.f + __expf(-fabsf(x - y) * inv_tau));
+  const float d = fminf(fabsf(x - y), 1e30f);
+  return fmaf(c.k2, lg2a(1.f + ex2a(-d * c.k1)), mx);
 }
 
 // Lane-side constants of the forward layout (lane l holds successor states
 // j = R l + r; predecessors 2j, 2j + 1 mod S).
-template <int R>
+template <int R, int B>
 struct FwdLane {
-  float sA[R][4], sB[R][4];  // branch signs from 2j (A) and 2j + 1 (B)
+  float sA[R][B], sB[R][B];  // branch signs from 2j (A) and 2j + 1 (B)
   int la, lb;                // source lanes of the predecessors
   bool live;
   __device__ void init(const MArgs& a, int lane) {
@@ -89,8 +137,8 @@ struct FwdLane {
 #pragma unroll
     for (int r = 0; r < R; r++) {
       const uint32_t j = (uint32_t)(R * lane + r);
-      signs(a, aout_m(a, 2u * j), sA[r]);
-      signs(a, aout_m(a, 2u * j + 1u), sB[r]);
+      signs<B>(aout_m(a, 2u * j), sA[r]);
+      signs<B>(aout_m(a, 2u * j + 1u), sB[r]);
     }
     if (R == 1) {
       la = (2 * lane) & (a.S - 1);
@@ -103,10 +151,18 @@ struct FwdLane {
 };
 
 // One forward stage (Eq. 3 in max-plus or log-sum-exp form) on the lane's
-// metrics m; hard: returns the ballots of the decisions in bal.
-template <int R, bool SOFT>
-__device__ __forceinline__ void fwd_step(float (&m)[R], const float (&l)[4], const FwdLane<R>& fl, float tau,
-                                         float inv_tau, uint32_t (&bal)[R]) {
+// metrics m; hard: returns the ballots of the decisions in bal.  The branch
+// metrics depend only on the LLRs, so they are formed while the shuffles of
+// the metrics are in flight.
+template <int R, int B, bool SOFT>
+__device__ __forceinline__ void fwd_step(float (&m)[R], const float (&l)[B], const FwdLane<R, B>& fl, const Lse& c,
+                                         uint32_t (&bal)[R]) {
+  float da[R], db[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    da[r] = bmv<B>(fl.sA[r], l);
+    db[r] = bmv<B>(fl.sB[r], l);
+  }
   float qa[R], qb[R];
 #pragma unroll
   for (int r = 0; r < R; r++) {
@@ -123,9 +179,9 @@ __device__ __forceinline__ void fwd_step(float (&m)[R], const float (&l)[4], con
       p0 = (2 * r < R) ? qa[2 * r] : qb[2 * r - R];
       p1 = (2 * r < R) ? qa[2 * r + 1] : qb[2 * r - R + 1];
     }
-    const float x0 = p0 + bm4(fl.sA[r], l), x1 = p1 + bm4(fl.sB[r], l);
+    const float x0 = p0 + da[r], x1 = p1 + db[r];
     if constexpr (SOFT) {
-      m[r] = lse2(x0, x1, tau, inv_tau);
+      m[r] = lse2(x0, x1, c);
       bal[r] = 0u;
     } else {
       const bool d = x1 > x0;  // ties keep the lower predecessor
@@ -136,58 +192,85 @@ __device__ __forceinline__ void fwd_step(float (&m)[R], const float (&l)[4], con
 }
 
 // The frame's LLRs of stages [i0, i0 + 32): lane k loads stage i0 + k.
-__device__ __forceinline__ void load_block(const MArgs& a, const float* llr, int64_t i0, int lane, float (&lv)[4]) {
+template <int B>
+__device__ __forceinline__ void load_block(const MArgs& a, const float* llr, int64_t i0, int lane, float (&lv)[B]) {
+  const bool in = i0 + lane < a.n;
 #pragma unroll
-  for (int b = 0; b < 4; b++) lv[b] = (b < a.beta && i0 + lane < a.n) ? llr[(i0 + lane) * a.beta + b] : 0.f;
+  for (int b = 0; b < B; b++) lv[b] = in ? llr[(i0 + lane) * B + b] : 0.f;
 }
 
-__device__ __forceinline__ void stage_llr(const float (&lv)[4], int k, float (&l)[4]) {
+template <int B>
+__device__ __forceinline__ void stage_llr(const float (&lv)[B], int k, float (&l)[B]) {
 #pragma unroll
-  for (int b = 0; b < 4; b++) l[b] = __shfl_sync(0xffffffffu, lv[b], k);
+  for (int b = 0; b < B; b++) l[b] = __shfl_sync(0xffffffffu, lv[b], k);
 }
 
-template <int R, bool SOFT>
+// Runs body(k) for k = 0 .. cnt-1 (ascending) or cnt-1 .. 0 (descending).
+// kFull: unrolled with constant k for whole blocks of 32 and guarded for a
+// partial one (small bodies, R <= 2); otherwise a loop unrolled by four.
+template <bool kDown, bool kFull, class F>
+__device__ __forceinline__ void block_stages(int cnt, F&& body) {
+  if constexpr (kFull) {
+    if (cnt == 32) {
+#pragma unroll
+      for (int q = 0; q < 32; q++) body(kDown ? 31 - q : q);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; q++) {
+        const int k = kDown ? 31 - q : q;
+        if (k < cnt) body(k);
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int q = 0; q < cnt; q++) body(kDown ? cnt - 1 - q : q);
+  }
+}
+
+template <int R, int B, bool SOFT>
 __global__ void __launch_bounds__(kWarps * 32) metric_fwd_kernel(const MArgs a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int f = blockIdx.x * kWarps + w;
   if (f >= a.F) return;
   const int S = a.S;
-  const float tau = a.tau, inv_tau = SOFT ? 1.f / a.tau : 0.f;
-  FwdLane<R> fl;
+  const Lse c(SOFT ? a.tau : 1.f);
+  FwdLane<R, B> fl;
   fl.init(a, lane);
   float m[R];
 #pragma unroll
   for (int r = 0; r < R; r++) m[r] = (R * lane + r == 0) ? 0.f : -INFINITY;  // 0-rooted
-  const float* llr = a.llr + (int64_t)f * a.n * a.beta;
+  const float* llr = a.llr + (int64_t)f * a.n * B;
   uint8_t* ws = a.ws + (int64_t)f * a.ws_frame;
   double off = 0.0;
   int64_t next_ck = 0;  // next checkpointed stage (soft)
   float* ck = (float*)ws;
+  double* cko = (double*)(ws + soft_offsets_at(a.nck, a.C, S));
   for (int64_t i0 = 0; i0 < a.n; i0 += 32) {
-    float lv[4];
-    load_block(a, llr, i0, lane, lv);
+    float lv[B];
+    load_block<B>(a, llr, i0, lane, lv);
     const int cnt = (a.n - i0 < 32) ? (int)(a.n - i0) : 32;
     uint32_t keep[R];
 #pragma unroll
     for (int r = 0; r < R; r++) keep[r] = 0u;
-    for (int k = 0; k < cnt; k++) {
-      const int64_t t = i0 + k;
-      if (SOFT && t == next_ck) {  // checkpoint of the metrics entering stage t
+    block_stages<false, (R <= 2)>(cnt, [&](int k) {
+      if (SOFT && i0 + k == next_ck) {  // checkpoint of the metrics entering this stage, and its offset
 #pragma unroll
         for (int r = 0; r < R; r++)
           if (fl.live) ck[R * lane + r] = m[r];
+        if (lane == 0) *cko = off;
         ck += S;
+        cko++;
         next_ck += a.C;
       }
-      float l[4];
-      stage_llr(lv, k, l);
+      float l[B];
+      stage_llr<B>(lv, k, l);
       uint32_t bal[R];
-      fwd_step<R, SOFT>(m, l, fl, tau, inv_tau, bal);
+      fwd_step<R, B, SOFT>(m, l, fl, c, bal);
       if (!SOFT) {
 #pragma unroll
         for (int r = 0; r < R; r++) keep[r] = (lane == k) ? bal[r] : keep[r];
       }
-    }
+    });
     if (!SOFT && i0 + lane < a.n) {
       uint32_t* dw = (uint32_t*)ws + (i0 + lane) * R;
 #pragma unroll
@@ -199,23 +282,33 @@ __global__ void __launch_bounds__(kWarps * 32) metric_fwd_kernel(const MArgs a) 
     for (int r = 0; r < R; r++) m[r] -= ref;
     off += (double)ref;
   }
-  if (lane == 0) a.metric[f] = (float)(off + (double)m[0]);
+  if (lane == 0) {
+    const double M = off + (double)m[0];
+    a.metric[f] = (float)M;
+    if (SOFT) *(double*)(ws + soft_offsets_at(a.nck, a.C, S) + (size_t)a.nck * sizeof(double)) = M;
+  }
 }
 
 // hard backward: traceback from state 0 through the stored decisions (every
-// lane follows the same state; lane k holds stage b0 + k's words), then the
-// +-1 branch symbols times the upstream gradient, one stage per lane
-template <int R>
+// lane follows the same state), then the +-1 branch symbols times the
+// upstream gradient, one stage per lane.  Lane k holds stage b0 + k's words;
+// for R <= 2 every lane takes the block's words by shuffle before the chain
+// starts (they do not depend on the state), so a step of the chain is a
+// register select, a shift and an add; for R >= 4 the words go through shared
+// memory.
+template <int R, int B>
 __global__ void __launch_bounds__(kWarps * 32) metric_bwd_hard_kernel(const MArgs a) {
+  constexpr int RS = R > 2 ? R : 1;
+  __shared__ uint32_t sw[kWarps][32][RS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int f = blockIdx.x * kWarps + w;
   if (f >= a.F) return;
   const uint32_t S = (uint32_t)a.S;
   const uint32_t* dw = (const uint32_t*)(a.ws + (int64_t)f * a.ws_frame);
   const float g = a.gmet[f];
-  float* grad = a.grad + (int64_t)f * a.n * a.beta;
+  float* grad = a.grad + (int64_t)f * a.n * B;
   uint32_t J = 0;  // state after the last stage (terminated)
-  uint32_t wn[R];   // the next (lower) block's words, loaded one block ahead
+  uint32_t wn[R];  // the next (lower) block's words, loaded one block ahead
   {
     const int64_t my = ((a.n - 1) / 32) * 32 + lane;
 #pragma unroll
@@ -231,21 +324,36 @@ __global__ void __launch_bounds__(kWarps * 32) metric_bwd_hard_kernel(const MArg
     }
     const int top = (a.n - b0 < 32) ? (int)(a.n - b0) : 32;
     uint32_t myR = 0;
-    for (int k = top - 1; k >= 0; k--) {
-      uint32_t sel = wv[0];
+    if constexpr (R <= 2) {
+      uint32_t W[32][R];
 #pragma unroll
-      for (int r = 1; r < R; r++) sel = ((J & (uint32_t)(R - 1)) == (uint32_t)r) ? wv[r] : sel;
-      const uint32_t word = __shfl_sync(0xffffffffu, sel, k);
-      const uint32_t d = (word >> (J / R)) & 1u;
-      const uint32_t Rw = 2u * J + d;  // the branch's register word: predecessor (Rw mod S) -> J
-      myR = (lane == k) ? Rw : myR;
-      J = Rw & (S - 1u);
+      for (int k = 0; k < 32; k++)
+#pragma unroll
+        for (int r = 0; r < R; r++) W[k][r] = __shfl_sync(0xffffffffu, wv[r], k);
+      block_stages<true, true>(top, [&](int k) {
+        const uint32_t word = (R == 1) ? W[k][0] : ((J & 1u) ? W[k][R - 1] : W[k][0]);
+        const uint32_t d = (word >> (J / R)) & 1u;
+        const uint32_t Rw = 2u * J + d;  // the branch's register word: predecessor (Rw mod S) -> J
+        myR = (lane == k) ? Rw : myR;
+        J = Rw & (S - 1u);
+      });
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; r++) sw[w][lane][r] = wv[r];
+      __syncwarp();
+      block_stages<true, false>(top, [&](int k) {
+        const uint32_t word = sw[w][k][J & (uint32_t)(R - 1)];
+        const uint32_t d = (word >> (J / R)) & 1u;
+        const uint32_t Rw = 2u * J + d;
+        myR = (lane == k) ? Rw : myR;
+        J = Rw & (S - 1u);
+      });
+      __syncwarp();
     }
     if (my < a.n) {
       const uint32_t o = aout_m(a, myR);
 #pragma unroll
-      for (int b = 0; b < 4; b++)
-        if (b < a.beta) grad[my * a.beta + b] = ((o >> b) & 1u) ? -g : g;
+      for (int b = 0; b < B; b++) grad[my * B + b] = ((o >> b) & 1u) ? -g : g;
     }
   }
 }
@@ -254,7 +362,7 @@ __global__ void __launch_bounds__(kWarps * 32) metric_bwd_hard_kernel(const MArg
 // states i = R l + r (successors i >> 1 and (i >> 1) + S/2, from lanes l >> 1
 // and (l >> 1) + 16 -- or + S/2 when R = 1), the alphas of each segment of C
 // stages recomputed from its checkpoint into the workspace
-template <int R>
+template <int R, int B>
 __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const MArgs a) {
   // [warp][stage of the block][source lane * 5 + (z, g0..g3)]: 165 floats a
   // row, so both the row writes and the column sums are free of bank conflicts
@@ -263,27 +371,31 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
   const int f = blockIdx.x * kWarpsSoft + w;
   if (f >= a.F) return;
   const int S = a.S;
-  const float tau = a.tau, inv_tau = 1.f / a.tau;
+  const Lse c(a.tau);
   const float g = a.gmet[f];
-  const float* llr = a.llr + (int64_t)f * a.n * a.beta;
-  float* grad = a.grad + (int64_t)f * a.n * a.beta;
-  float* ck = (float*)(a.ws + (int64_t)f * a.ws_frame);
+  const float* llr = a.llr + (int64_t)f * a.n * B;
+  float* grad = a.grad + (int64_t)f * a.n * B;
+  uint8_t* wsf = a.ws + (int64_t)f * a.ws_frame;
+  float* ck = (float*)wsf;
   float* seg = ck + a.nck * S;  // C rows: alpha entering stage t0 + row
-  FwdLane<R> fl;
+  const double* cko = (const double*)(wsf + soft_offsets_at(a.nck, a.C, S));
+  const double Mtau = cko[a.nck];
+  FwdLane<R, B> fl;
   fl.init(a, lane);
   // backward-layout constants: branch signs from the lane's states
   const bool live = R * lane < S;
-  float s0[R][4], s1[R][4];
+  float s0[R][B], s1[R][B];
 #pragma unroll
   for (int r = 0; r < R; r++) {
     const uint32_t i = (uint32_t)(R * lane + r);
-    signs(a, aout_m(a, i), s0[r]);
-    signs(a, aout_m(a, (uint32_t)S + i), s1[r]);
+    signs<B>(aout_m(a, i), s0[r]);
+    signs<B>(aout_m(a, (uint32_t)S + i), s1[r]);
   }
   const int src0 = lane >> 1, src1 = (R == 1) ? (lane >> 1) + S / 2 : (lane >> 1) + 16;
   float bt[R];  // beta of the lane's states after the current stage
 #pragma unroll
   for (int r = 0; r < R; r++) bt[r] = (R * lane + r == 0) ? 0.f : -INFINITY;  // terminated in state 0
+  double boff = 0.0;  // sum of the re-reference offsets taken out of bt
   float (*rd)[32 * 5 + 5] = red[w];
   for (int64_t sgi = a.nck - 1; sgi >= 0; sgi--) {
     const int64_t t0 = sgi * a.C;
@@ -294,24 +406,26 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
 #pragma unroll
       for (int r = 0; r < R; r++) m[r] = fl.live ? ck[sgi * S + R * lane + r] : -INFINITY;
       for (int64_t b = t0; b < t1; b += 32) {
-        float lv[4];
-        load_block(a, llr, b, lane, lv);
+        float lv[B];
+        load_block<B>(a, llr, b, lane, lv);
         const int cnt = (t1 - b < 32) ? (int)(t1 - b) : 32;
-        for (int k = 0; k < cnt; k++) {
+        block_stages<false, (R <= 2)>(cnt, [&](int k) {
           const int64_t t = b + k;
 #pragma unroll
           for (int r = 0; r < R; r++)
             if (fl.live) seg[(t - t0) * S + R * lane + r] = m[r];
           if (t + 1 < t1) {
-            float l[4];
-            stage_llr(lv, k, l);
+            float l[B];
+            stage_llr<B>(lv, k, l);
             uint32_t bal[R];
-            fwd_step<R, true>(m, l, fl, tau, inv_tau, bal);
+            fwd_step<R, B, true>(m, l, fl, c, bal);
           }
-        }
+        });
       }
     }
     __syncwarp();
+    // M_tau less the offset of this segment's alphas
+    const double mrel = Mtau - cko[sgi];
     // beta recursion and posteriors, 32 stages at a time from the top; the
     // lane's alphas of the stage below are loaded one stage ahead
     float aln[R];
@@ -319,17 +433,26 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
     for (int r = 0; r < R; r++) aln[r] = live ? seg[(t1 - 1 - t0) * S + R * lane + r] : -INFINITY;
     for (int64_t hi = t1; hi > t0; hi -= 32) {
       const int64_t lo = (hi - 32 > t0) ? hi - 32 : t0;
-      float lv[4];
-      load_block(a, llr, lo, lane, lv);
-      for (int64_t t = hi - 1; t >= lo; t--) {
-        const int k = (int)(t - lo);
-        float l[4];
-        stage_llr(lv, k, l);
+      float lv[B];
+      load_block<B>(a, llr, lo, lane, lv);
+      // the posteriors' common reference, in base-2 exponent units
+      const float refk = (float)((mrel - boff) * (double)c.k1);
+      float bmx = -INFINITY;
+      block_stages<true, (R <= 2)>((int)(hi - lo), [&](int k) {
+        const int64_t t = lo + k;
+        float l[B];
+        stage_llr<B>(lv, k, l);
         float al[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
           al[r] = aln[r];
           aln[r] = (live && t - 1 >= t0) ? seg[(t - 1 - t0) * S + R * lane + r] : -INFINITY;
+        }
+        float e0[R], e1[R];  // branch metrics, formed while the shuffles are in flight
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          e0[r] = bmv<B>(s0[r], l);
+          e1[r] = bmv<B>(s1[r], l);
         }
         float v0[R], v1[R];
 #pragma unroll
@@ -337,8 +460,9 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
           v0[r] = __shfl_sync(0xffffffffu, bt[r], src0);
           v1[r] = __shfl_sync(0xffffffffu, bt[r], src1);
         }
-        float u0[R], u1[R];
-        float mx = -INFINITY;
+        float z = 0.f, gb[B];
+#pragma unroll
+        for (int b = 0; b < B; b++) gb[b] = 0.f;
 #pragma unroll
         for (int r = 0; r < R; r++) {
           // successors of i = R l + r: j0 = i >> 1 in register (l & 1) * R/2 + r/2 of
@@ -352,53 +476,48 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
             bj0 = (lane & 1) ? v0[rb] : v0[ra];
             bj1 = (lane & 1) ? v1[rb] : v1[ra];
           }
-          u0[r] = bm4(s0[r], l) + bj0;
-          u1[r] = bm4(s1[r], l) + bj1;
-          if (live) mx = fmaxf(mx, fmaxf(al[r] + u0[r], al[r] + u1[r]));
-        }
+          const float u0 = e0[r] + bj0, u1 = e1[r] + bj1;
+          // al = -inf on dead lanes, so their posteriors are 0
+          const float q0 = ex2a(fmaf(al[r] + u0, c.k1, -refk));
+          const float q1 = ex2a(fmaf(al[r] + u1, c.k1, -refk));
+          z += q0 + q1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        float z = 0.f, gb[4] = {0.f, 0.f, 0.f, 0.f};
-        float bmx = -INFINITY;
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-          if (live) {
-            const float q0 = __expf((al[r] + u0[r] - mx) * inv_tau);
-            const float q1 = __expf((al[r] + u1[r] - mx) * inv_tau);
-            z += q0 + q1;
-#pragma unroll
-            for (int b = 0; b < 4; b++) gb[b] += q0 * s0[r][b] + q1 * s1[r][b];
-          }
-          bt[r] = live ? lse2(u0[r], u1[r], tau, inv_tau) : -INFINITY;
-          bmx = fmaxf(bmx, bt[r]);
+          for (int b = 0; b < B; b++) gb[b] = fmaf(q0, s0[r][b], fmaf(q1, s1[r][b], gb[b]));
+          bt[r] = live ? lse2(u0, u1, c) : -INFINITY;
         }
         float* cell = &rd[k][lane * 5];
         cell[0] = z;
 #pragma unroll
-        for (int b = 0; b < 4; b++) cell[1 + b] = gb[b];
-        // re-reference beta to the lane-0 state 0 value every 32 stages
+        for (int b = 0; b < B; b++) cell[1 + b] = gb[b];
         if (k == 0) {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) bmx = fmaxf(bmx, __shfl_xor_sync(0xffffffffu, bmx, o));
-          if (bmx != -INFINITY) {
-#pragma unroll
-            for (int r = 0; r < R; r++) bt[r] -= bmx;
-          }
+          for (int r = 0; r < R; r++) bmx = fmaxf(bmx, bt[r]);
         }
+      });
+      // re-reference beta to its maximum every 32 stages
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bmx = fmaxf(bmx, __shfl_xor_sync(0xffffffffu, bmx, o));
+      if (bmx != -INFINITY) {
+#pragma unroll
+        for (int r = 0; r < R; r++) bt[r] -= bmx;
+        boff += (double)bmx;
       }
       __syncwarp();
       // lane k sums stage lo + k over the lanes and writes its gradient
       if (lo + lane < hi) {
-        float z = 0.f, gb[4] = {0.f, 0.f, 0.f, 0.f};
+        float z = 0.f, gb[B];
+#pragma unroll
+        for (int b = 0; b < B; b++) gb[b] = 0.f;
+#pragma unroll 8
         for (int q = 0; q < 32; q++) {
           const float* cell = &rd[lane][q * 5];
           z += cell[0];
 #pragma unroll
-          for (int b = 0; b < 4; b++) gb[b] += cell[1 + b];
+          for (int b = 0; b < B; b++) gb[b] += cell[1 + b];
         }
+        const float gz = g / z;
 #pragma unroll
-        for (int b = 0; b < 4; b++)
-          if (b < a.beta) grad[(lo + lane) * a.beta + b] = g * gb[b] / z;
+        for (int b = 0; b < B; b++) grad[(lo + lane) * B + b] = gb[b] * gz;
       }
       __syncwarp();
     }
@@ -412,7 +531,7 @@ size_t frame_bytes(const vit_code* c, int64_t n, float tau, int C) {
   const int S = 1 << (c->K - 1);
   if (tau > 0.f) {
     const int64_t nck = (n + C - 1) / C;
-    return align_up((size_t)(nck + C) * S * sizeof(float));
+    return align_up(soft_offsets_at(nck, C, S) + (size_t)(nck + 1) * sizeof(double));
   }
   return align_up((size_t)n * ((S + 31) / 32) * sizeof(uint32_t));
 }
@@ -438,6 +557,42 @@ int fill(MArgs& a, const vit_code* c, int F, int64_t n, float tau, int C) {
   return VIT_OK;
 }
 
+// Launches one kernel of the (R, beta) family: which 0 = forward, 1 = hard
+// backward, 2 = soft backward.
+template <int R, int B>
+void launch_rb(int which, bool soft, const MArgs& a, cudaStream_t s) {
+  const unsigned grid = (unsigned)((a.F + kWarps - 1) / kWarps);
+  if (which == 0) {
+    if (soft)
+      metric_fwd_kernel<R, B, true><<<grid, kWarps * 32, 0, s>>>(a);
+    else
+      metric_fwd_kernel<R, B, false><<<grid, kWarps * 32, 0, s>>>(a);
+  } else if (which == 1) {
+    metric_bwd_hard_kernel<R, B><<<grid, kWarps * 32, 0, s>>>(a);
+  } else {
+    const unsigned gs = (unsigned)((a.F + kWarpsSoft - 1) / kWarpsSoft);
+    metric_bwd_soft_kernel<R, B><<<gs, kWarpsSoft * 32, 0, s>>>(a);
+  }
+}
+
+template <int B>
+void launch_b(int which, bool soft, const MArgs& a, cudaStream_t s) {
+  switch (a.spl) {
+    case 1: launch_rb<1, B>(which, soft, a, s); break;
+    case 2: launch_rb<2, B>(which, soft, a, s); break;
+    case 4: launch_rb<4, B>(which, soft, a, s); break;
+    default: launch_rb<8, B>(which, soft, a, s); break;
+  }
+}
+
+void launch(int which, bool soft, const MArgs& a, cudaStream_t s) {
+  switch (a.beta) {
+    case 2: launch_b<2>(which, soft, a, s); break;
+    case 3: launch_b<3>(which, soft, a, s); break;
+    default: launch_b<4>(which, soft, a, s); break;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -458,19 +613,7 @@ int vit_metric_fwd(const vit_code* c, const float* llr, int nframes, int64_t n, 
   a.llr = llr;
   a.metric = metric_out;
   a.ws = (uint8_t*)ws;
-  const unsigned grid = (unsigned)((nframes + kWarps - 1) / kWarps);
-  cudaStream_t s = (cudaStream_t)stream;
-  const bool soft = tau > 0.f;
-  switch (a.spl) {
-    case 1: soft ? metric_fwd_kernel<1, true><<<grid, kWarps * 32, 0, s>>>(a)
-                 : metric_fwd_kernel<1, false><<<grid, kWarps * 32, 0, s>>>(a); break;
-    case 2: soft ? metric_fwd_kernel<2, true><<<grid, kWarps * 32, 0, s>>>(a)
-                 : metric_fwd_kernel<2, false><<<grid, kWarps * 32, 0, s>>>(a); break;
-    case 4: soft ? metric_fwd_kernel<4, true><<<grid, kWarps * 32, 0, s>>>(a)
-                 : metric_fwd_kernel<4, false><<<grid, kWarps * 32, 0, s>>>(a); break;
-    default: soft ? metric_fwd_kernel<8, true><<<grid, kWarps * 32, 0, s>>>(a)
-                  : metric_fwd_kernel<8, false><<<grid, kWarps * 32, 0, s>>>(a); break;
-  }
+  launch(0, tau > 0.f, a, (cudaStream_t)stream);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return vit::set_error(VIT_ECUDA, "metric forward launch: %s", cudaGetErrorString(e));
   return VIT_OK;
@@ -488,24 +631,8 @@ int vit_metric_bwd(const vit_code* c, const float* llr, const float* grad_metric
   a.gmet = grad_metric;
   a.grad = grad_llr;
   a.ws = (uint8_t*)const_cast<void*>(ws);
-  const unsigned grid = (unsigned)((nframes + kWarps - 1) / kWarps);
-  cudaStream_t s = (cudaStream_t)stream;
-  if (tau > 0.f) {
-    const unsigned gs = (unsigned)((nframes + kWarpsSoft - 1) / kWarpsSoft);
-    switch (a.spl) {
-      case 1: metric_bwd_soft_kernel<1><<<gs, kWarpsSoft * 32, 0, s>>>(a); break;
-      case 2: metric_bwd_soft_kernel<2><<<gs, kWarpsSoft * 32, 0, s>>>(a); break;
-      case 4: metric_bwd_soft_kernel<4><<<gs, kWarpsSoft * 32, 0, s>>>(a); break;
-      default: metric_bwd_soft_kernel<8><<<gs, kWarpsSoft * 32, 0, s>>>(a); break;
-    }
-  } else {
-    switch (a.spl) {
-      case 1: metric_bwd_hard_kernel<1><<<grid, kWarps * 32, 0, s>>>(a); break;
-      case 2: metric_bwd_hard_kernel<2><<<grid, kWarps * 32, 0, s>>>(a); break;
-      case 4: metric_bwd_hard_kernel<4><<<grid, kWarps * 32, 0, s>>>(a); break;
-      default: metric_bwd_hard_kernel<8><<<grid, kWarps * 32, 0, s>>>(a); break;
-    }
-  }
+  const bool soft = tau > 0.f;
+  launch(soft ? 2 : 1, soft, a, (cudaStream_t)stream);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return vit::set_error(VIT_ECUDA, "metric backward launch: %s", cudaGetErrorString(e));
   return VIT_OK;

@@ -90,3 +90,52 @@ def test_finite_differences_fp64(vit, tau):
         assert g[i, t, b] == pytest.approx(fd, rel=1e-4, abs=1e-4), (i, t, b, tau)
         checked += 1
     assert checked >= 30, (checked, skipped)
+
+
+# Codes of every (states per lane, beta) family the kernels are compiled for:
+# R = 1 with S < 32 and S = 32, R = 2, 4 and 8; beta = 2, 3, 4.
+OTHER_CODES = [
+    (3, 2, (0o7, 0o5)),
+    (4, 4, (0o13, 0o15, 0o15, 0o17)),
+    (5, 3, (0o25, 0o33, 0o37)),
+    (6, 2, (0o53, 0o75)),
+    (7, 3, (0o133, 0o171, 0o165)),
+    (8, 2, (0o247, 0o371)),
+    (9, 2, (0o561, 0o753)),
+    (9, 4, (0o463, 0o535, 0o733, 0o745)),
+]
+
+
+@pytest.mark.parametrize("code", OTHER_CODES, ids=lambda c: f"K{c[0]}b{c[1]}")
+@pytest.mark.parametrize("tau", [0.0, 1.0])
+def test_metric_other_codes(vit, code, tau):
+    k, beta, polys = code
+    _, llr = synth.float_frames(lambda x: oracle.encode(k, beta, polys, x), beta, k, 6, 90, 2.0, seed=12)
+    c = vit.Code(k, beta, polys)
+    x = torch.from_numpy(llr).cuda().requires_grad_(True)
+    m = vit.path_metric(x, c, tau, 16)
+    m.sum().backward()
+    torch.cuda.synchronize()
+    got_m = m.detach().cpu().numpy().astype(np.float64)
+    got_g = x.grad.cpu().numpy().astype(np.float64)
+    x64 = llr.astype(np.float64)
+    if tau == 0.0:
+        want_m, want_g = oracle.metric_hard(k, beta, polys, x64)
+        np.testing.assert_allclose(got_m, want_m, rtol=1e-5, atol=1e-4)
+        assert np.mean(got_g != want_g) < 1e-2
+    else:
+        want_m, want_g = oracle.metric_lse(k, beta, polys, x64, tau)
+        np.testing.assert_allclose(got_m, want_m, rtol=1e-5, atol=1e-4)
+        np.testing.assert_allclose(got_g, want_g, rtol=1e-3, atol=2e-4)
+
+
+def test_soft_gradient_small_tau(vit):
+    # tau = 0.05 sharpens the posteriors towards the best path; the reference
+    # taken from the forward metric must keep every exponent finite
+    _, llr = _frames(4, 256, 2.0, seed=13)
+    up = np.ones(4, np.float32)
+    m, g = _run(vit, llr, 0.05, g=up)
+    want_m, want_g = oracle.metric_lse(K, BETA, POLYS, llr.astype(np.float64), 0.05)
+    assert np.all(np.isfinite(g))
+    np.testing.assert_allclose(m, want_m, rtol=1e-5)
+    np.testing.assert_allclose(g, want_g, rtol=1e-3, atol=2e-3)
