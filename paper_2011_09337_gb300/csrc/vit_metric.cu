@@ -20,8 +20,10 @@
 // (bit l of word r = state R l + r), stored per block of 32 stages.  The soft
 // backward checkpoints alpha every C stages, recomputes a segment's alphas
 // from its checkpoint, and runs the beta recursion with lanes holding
-// predecessor states; the per-stage gradient sums go through shared memory,
-// one stage per lane, 32 stages at a time.
+// predecessor states (segment alphas in shared memory when they fit); the
+// per-stage gradient sums go through shared memory, one stage per lane, 32
+// stages at a time.  Each block's LLRs are loaded one block ahead, and each
+// stage's LLRs are shuffled out one stage ahead.
 //
 // Log-sum-exp in base 2: tau log(e^{x/tau} + e^{y/tau}) = max(x, y) +
 // tau ln2 log2(1 + 2^{-|x - y| log2(e) / tau}), with the hardware base-2
@@ -47,7 +49,6 @@
 namespace {
 
 constexpr int kWarps = 4;      // frames per CTA (forward, hard backward)
-constexpr int kWarpsSoft = 2;  // frames per CTA of the soft backward (its shared reduction buffer)
 constexpr float kLog2e = 1.4426950408889634f;  // log2(e)
 constexpr float kLn2 = 0.6931471805599453f;    // ln(2)
 
@@ -245,32 +246,52 @@ __global__ void __launch_bounds__(kWarps * 32) metric_fwd_kernel(const MArgs a) 
   int64_t next_ck = 0;  // next checkpointed stage (soft)
   float* ck = (float*)ws;
   double* cko = (double*)(ws + soft_offsets_at(a.nck, a.C, S));
+  const bool ck_blocks = (a.C % 32) == 0;
+  float lv[B];
+  load_block<B>(a, llr, 0, lane, lv);
   for (int64_t i0 = 0; i0 < a.n; i0 += 32) {
-    float lv[B];
-    load_block<B>(a, llr, i0, lane, lv);
+    float lvn[B];  // the next block's LLRs, loaded one block ahead
+    load_block<B>(a, llr, i0 + 32, lane, lvn);
     const int cnt = (a.n - i0 < 32) ? (int)(a.n - i0) : 32;
     uint32_t keep[R];
 #pragma unroll
     for (int r = 0; r < R; r++) keep[r] = 0u;
-    block_stages<false, (R <= 2)>(cnt, [&](int k) {
-      if (SOFT && i0 + k == next_ck) {  // checkpoint of the metrics entering this stage, and its offset
+    float l[B];
+    stage_llr<B>(lv, 0, l);
+    auto checkpoint = [&]() {  // the metrics entering stage next_ck, and their offset
 #pragma unroll
-        for (int r = 0; r < R; r++)
-          if (fl.live) ck[R * lane + r] = m[r];
-        if (lane == 0) *cko = off;
-        ck += S;
-        cko++;
-        next_ck += a.C;
-      }
-      float l[B];
-      stage_llr<B>(lv, k, l);
+      for (int r = 0; r < R; r++)
+        if (fl.live) ck[R * lane + r] = m[r];
+      if (lane == 0) *cko = off;
+      ck += S;
+      cko++;
+      next_ck += a.C;
+    };
+    auto stage = [&](int k) {
+      float ln[B];  // the next stage's LLRs (lane 32 reads lane 0: unused)
+      stage_llr<B>(lv, k + 1, ln);
       uint32_t bal[R];
       fwd_step<R, B, SOFT>(m, l, fl, c, bal);
       if (!SOFT) {
 #pragma unroll
         for (int r = 0; r < R; r++) keep[r] = (lane == k) ? bal[r] : keep[r];
       }
-    });
+#pragma unroll
+      for (int b = 0; b < B; b++) l[b] = ln[b];
+    };
+    if (!SOFT || ck_blocks) {
+      // checkpoints (C a multiple of 32) fall on block starts: the block's
+      // stages form one branch-free sequence
+      if (SOFT && i0 == next_ck) checkpoint();
+      block_stages<false, (R <= 2)>(cnt, stage);
+    } else {
+      block_stages<false, (R <= 2)>(cnt, [&](int k) {
+        if (i0 + k == next_ck) checkpoint();
+        stage(k);
+      });
+    }
+#pragma unroll
+    for (int b = 0; b < B; b++) lv[b] = lvn[b];
     if (!SOFT && i0 + lane < a.n) {
       uint32_t* dw = (uint32_t*)ws + (i0 + lane) * R;
 #pragma unroll
@@ -361,14 +382,30 @@ __global__ void __launch_bounds__(kWarps * 32) metric_bwd_hard_kernel(const MArg
 // soft backward: beta recursion from the end with lanes holding predecessor
 // states i = R l + r (successors i >> 1 and (i >> 1) + S/2, from lanes l >> 1
 // and (l >> 1) + 16 -- or + S/2 when R = 1), the alphas of each segment of C
-// stages recomputed from its checkpoint into the workspace
+// stages recomputed from its checkpoint into shared memory when C S floats
+// fit kSegSmemFloats, else into the workspace.  One warp per CTA; dynamic
+// shared memory: the reduction buffer, then the segment rows.
+//
+// Reduction buffer: [stage of the block][source lane * P + (z, g0..g_{B-1})],
+// P = B + 1 rounded up to odd and rows of 32 P + 1 floats, so the row writes
+// (lane stride P) and the column sums (row stride odd) are free of bank
+// conflicts.
+constexpr int kSegSmemFloats = 4096;
+template <int B>
+__host__ __device__ constexpr int red_stride() {
+  return ((B + 1) & 1) ? B + 1 : B + 2;
+}
+template <int B>
+__host__ __device__ constexpr int red_floats() {
+  return 32 * (32 * red_stride<B>() + 1);
+}
+
 template <int R, int B>
-__global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const MArgs a) {
-  // [warp][stage of the block][source lane * 5 + (z, g0..g3)]: 165 floats a
-  // row, so both the row writes and the column sums are free of bank conflicts
-  __shared__ float red[kWarpsSoft][32][32 * 5 + 5];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int f = blockIdx.x * kWarpsSoft + w;
+__global__ void __launch_bounds__(32) metric_bwd_soft_kernel(const MArgs a) {
+  extern __shared__ float dsm[];
+  constexpr int P = red_stride<B>(), ROW = 32 * P + 1;
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.x;
   if (f >= a.F) return;
   const int S = a.S;
   const Lse c(a.tau);
@@ -377,7 +414,9 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
   float* grad = a.grad + (int64_t)f * a.n * B;
   uint8_t* wsf = a.ws + (int64_t)f * a.ws_frame;
   float* ck = (float*)wsf;
-  float* seg = ck + a.nck * S;  // C rows: alpha entering stage t0 + row
+  // C rows: alpha entering stage t0 + row (generic pointer: shared or global)
+  float* seg = ((int64_t)a.C * S <= kSegSmemFloats) ? dsm + red_floats<B>() : ck + a.nck * S;
+  float* rd = dsm;
   const double* cko = (const double*)(wsf + soft_offsets_at(a.nck, a.C, S));
   const double Mtau = cko[a.nck];
   FwdLane<R, B> fl;
@@ -396,7 +435,6 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
 #pragma unroll
   for (int r = 0; r < R; r++) bt[r] = (R * lane + r == 0) ? 0.f : -INFINITY;  // terminated in state 0
   double boff = 0.0;  // sum of the re-reference offsets taken out of bt
-  float (*rd)[32 * 5 + 5] = red[w];
   for (int64_t sgi = a.nck - 1; sgi >= 0; sgi--) {
     const int64_t t0 = sgi * a.C;
     const int64_t t1 = (t0 + a.C < a.n) ? t0 + a.C : a.n;
@@ -405,22 +443,30 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
       float m[R];
 #pragma unroll
       for (int r = 0; r < R; r++) m[r] = fl.live ? ck[sgi * S + R * lane + r] : -INFINITY;
+      float lv[B];
+      load_block<B>(a, llr, t0, lane, lv);
       for (int64_t b = t0; b < t1; b += 32) {
-        float lv[B];
-        load_block<B>(a, llr, b, lane, lv);
+        float lvn[B];  // the next block's LLRs, one block ahead
+        load_block<B>(a, llr, b + 32, lane, lvn);
         const int cnt = (t1 - b < 32) ? (int)(t1 - b) : 32;
+        float l[B];
+        stage_llr<B>(lv, 0, l);
         block_stages<false, (R <= 2)>(cnt, [&](int k) {
           const int64_t t = b + k;
 #pragma unroll
           for (int r = 0; r < R; r++)
             if (fl.live) seg[(t - t0) * S + R * lane + r] = m[r];
-          if (t + 1 < t1) {
-            float l[B];
-            stage_llr<B>(lv, k, l);
-            uint32_t bal[R];
-            fwd_step<R, B, true>(m, l, fl, c, bal);
-          }
+          float ln[B];
+          stage_llr<B>(lv, k + 1, ln);
+          // (the step after the segment's last stage is computed and unused,
+          // which keeps the block free of branches)
+          uint32_t bal[R];
+          fwd_step<R, B, true>(m, l, fl, c, bal);
+#pragma unroll
+          for (int q = 0; q < B; q++) l[q] = ln[q];
         });
+#pragma unroll
+        for (int q = 0; q < B; q++) lv[q] = lvn[q];
       }
     }
     __syncwarp();
@@ -431,17 +477,26 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
     float aln[R];
 #pragma unroll
     for (int r = 0; r < R; r++) aln[r] = live ? seg[(t1 - 1 - t0) * S + R * lane + r] : -INFINITY;
+    const int64_t lo0 = (t1 - 32 > t0) ? t1 - 32 : t0;
+    float lv[B];
+    load_block<B>(a, llr, lo0, lane, lv);
     for (int64_t hi = t1; hi > t0; hi -= 32) {
       const int64_t lo = (hi - 32 > t0) ? hi - 32 : t0;
-      float lv[B];
-      load_block<B>(a, llr, lo, lane, lv);
+      const int cnt = (int)(hi - lo);
+      float lvn[B];  // the next (lower) block's LLRs, one block ahead
+      {
+        const int64_t lon = (lo - 32 > t0) ? lo - 32 : t0;
+        load_block<B>(a, llr, lon, lane, lvn);
+      }
       // the posteriors' common reference, in base-2 exponent units
       const float refk = (float)((mrel - boff) * (double)c.k1);
       float bmx = -INFINITY;
-      block_stages<true, (R <= 2)>((int)(hi - lo), [&](int k) {
+      float l[B];
+      stage_llr<B>(lv, cnt - 1, l);
+      block_stages<true, (R <= 2)>(cnt, [&](int k) {
         const int64_t t = lo + k;
-        float l[B];
-        stage_llr<B>(lv, k, l);
+        float ln[B];  // the next (lower) stage's LLRs (lane -1 reads lane 31: unused)
+        stage_llr<B>(lv, k - 1, ln);
         float al[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
@@ -462,7 +517,7 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
         }
         float z = 0.f, gb[B];
 #pragma unroll
-        for (int b = 0; b < B; b++) gb[b] = 0.f;
+        for (int q = 0; q < B; q++) gb[q] = 0.f;
 #pragma unroll
         for (int r = 0; r < R; r++) {
           // successors of i = R l + r: j0 = i >> 1 in register (l & 1) * R/2 + r/2 of
@@ -482,18 +537,22 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
           const float q1 = ex2a(fmaf(al[r] + u1, c.k1, -refk));
           z += q0 + q1;
 #pragma unroll
-          for (int b = 0; b < B; b++) gb[b] = fmaf(q0, s0[r][b], fmaf(q1, s1[r][b], gb[b]));
+          for (int q = 0; q < B; q++) gb[q] = fmaf(q0, s0[r][q], fmaf(q1, s1[r][q], gb[q]));
           bt[r] = live ? lse2(u0, u1, c) : -INFINITY;
         }
-        float* cell = &rd[k][lane * 5];
+        float* cell = rd + k * ROW + lane * P;
         cell[0] = z;
 #pragma unroll
-        for (int b = 0; b < B; b++) cell[1 + b] = gb[b];
+        for (int q = 0; q < B; q++) cell[1 + q] = gb[q];
         if (k == 0) {
 #pragma unroll
           for (int r = 0; r < R; r++) bmx = fmaxf(bmx, bt[r]);
         }
+#pragma unroll
+        for (int q = 0; q < B; q++) l[q] = ln[q];
       });
+#pragma unroll
+      for (int q = 0; q < B; q++) lv[q] = lvn[q];
       // re-reference beta to its maximum every 32 stages
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) bmx = fmaxf(bmx, __shfl_xor_sync(0xffffffffu, bmx, o));
@@ -504,23 +563,24 @@ __global__ void __launch_bounds__(kWarpsSoft * 32) metric_bwd_soft_kernel(const 
       }
       __syncwarp();
       // lane k sums stage lo + k over the lanes and writes its gradient
-      if (lo + lane < hi) {
+      if (lane < cnt) {
         float z = 0.f, gb[B];
 #pragma unroll
-        for (int b = 0; b < B; b++) gb[b] = 0.f;
+        for (int q = 0; q < B; q++) gb[q] = 0.f;
+        const float* row = rd + lane * ROW;
 #pragma unroll 8
-        for (int q = 0; q < 32; q++) {
-          const float* cell = &rd[lane][q * 5];
-          z += cell[0];
+        for (int j = 0; j < 32; j++) {
+          z += row[j * P];
 #pragma unroll
-          for (int b = 0; b < B; b++) gb[b] += cell[1 + b];
+          for (int q = 0; q < B; q++) gb[q] += row[j * P + 1 + q];
         }
         const float gz = g / z;
 #pragma unroll
-        for (int b = 0; b < B; b++) grad[(lo + lane) * B + b] = gb[b] * gz;
+        for (int q = 0; q < B; q++) grad[(lo + lane) * B + q] = gb[q] * gz;
       }
       __syncwarp();
     }
+    __syncwarp();
   }
 }
 
@@ -570,8 +630,12 @@ void launch_rb(int which, bool soft, const MArgs& a, cudaStream_t s) {
   } else if (which == 1) {
     metric_bwd_hard_kernel<R, B><<<grid, kWarps * 32, 0, s>>>(a);
   } else {
-    const unsigned gs = (unsigned)((a.F + kWarpsSoft - 1) / kWarpsSoft);
-    metric_bwd_soft_kernel<R, B><<<gs, kWarpsSoft * 32, 0, s>>>(a);
+    // one frame per CTA; the segment rows join the reduction buffer in
+    // shared memory when they fit (at most 36 KB, within the default limit)
+    static_assert((red_floats<B>() + kSegSmemFloats) * sizeof(float) <= 48 * 1024, "default shared-memory limit");
+    const size_t seg = ((int64_t)a.C * a.S <= kSegSmemFloats) ? (size_t)a.C * a.S : 0;
+    const size_t bytes = (red_floats<B>() + seg) * sizeof(float);
+    metric_bwd_soft_kernel<R, B><<<(unsigned)a.F, 32, bytes, s>>>(a);
   }
 }
 
