@@ -602,27 +602,39 @@ def metric_leg(vit, torch, device, steps, fp_rates, sm_mhz):
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     out = {"workload": METRIC_WORKLOAD, "frames": F, "stages_per_frame": n, "C": C}
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
     for tau in (0.0, 0.5, 1.0, 2.0):
+        # kernels: the C-ABI calls on preallocated buffers, back to back
+        ws = torch.empty(max(vit.metric_workspace(code, F, n, tau, C), 1), dtype=torch.uint8, device=device)
+        met = torch.empty(F, dtype=torch.float32, device=device)
+        gm = torch.ones(F, dtype=torch.float32, device=device)
+        gx = torch.empty_like(x)
+        for _ in range(3):
+            vit.metric_fwd(code, x, tau, C, met, ws)
+            vit.metric_bwd(code, x, gm, tau, C, ws, gx)
+        fwd_ms = timed(lambda: vit.metric_fwd(code, x, tau, C, met, ws), max(steps, 20))
+        bwd_ms = timed(lambda: vit.metric_bwd(code, x, gm, tau, C, ws, gx), max(steps, 20))
+        # the same through torch.autograd (ViterbiMetric), host overhead included
         xr = x.clone().requires_grad_(True)
         for _ in range(2):
             m = vit.path_metric(xr, code, tau, C)
-            (gx,) = torch.autograd.grad(m.sum(), xr)
-        torch.cuda.synchronize()
-        ev[0].record()
-        for _ in range(steps):
-            m = vit.path_metric(xr, code, tau, C)
-        ev[1].record()
-        torch.cuda.synchronize()
-        fwd_ms = ev[0].elapsed_time(ev[1]) / steps
-        ev[0].record()
-        for _ in range(steps):
-            (gx,) = torch.autograd.grad(m.sum(), xr, retain_graph=True)
-        ev[1].record()
-        torch.cuda.synchronize()
-        bwd_ms = ev[0].elapsed_time(ev[1]) / steps
+            (ga,) = torch.autograd.grad(m.sum(), xr)
+        af_ms = timed(lambda: vit.path_metric(xr, code, tau, C), max(steps, 20))
+        m = vit.path_metric(xr, code, tau, C)
+        ab_ms = timed(lambda: torch.autograd.grad(m.sum(), xr, retain_graph=True), max(steps, 20))
         key = "hard" if tau == 0.0 else f"tau_{tau:g}"
         r = {"fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "frames_per_s": F / ((fwd_ms + bwd_ms) * 1e-3),
-             "grad_finite": bool(torch.isfinite(gx).all().item())}
+             "autograd_fwd_ms": af_ms, "autograd_bwd_ms": ab_ms,
+             "grad_finite": bool(torch.isfinite(gx).all().item()),
+             "autograd_matches_kernels": bool(torch.equal(ga, gx))}
         if tau == 0.0:
             # 4 FP32 ops per state per stage (2 adds, compare, select) in the forward pass
             peak = max(fp_rates["fadd"], fp_rates["fmax"]) * 32 * sms * sm_mhz * 1e6
@@ -644,7 +656,7 @@ def metric_leg(vit, torch, device, steps, fp_rates, sm_mhz):
                                         "unit": "Tops/s", "frac": ach / peak,
                                         "ops": f"{nex:g} ex2 + {nlg:g} lg2 per state per stage"}
         out[key] = r
-        del xr, m, gx
+        del xr, m, gx, ga, ws
     return out
 
 
@@ -708,11 +720,11 @@ def large_streams_leg(vit, torch, device, steps):
     return out
 
 
-def profile_k9(vit, torch, device):
-    """Target of the K=9 ncu captures: one 2^25-bit stream decoded twice."""
+def profile_k9(vit, torch, device, log2_bits=25):
+    """Target of the K=9 ncu captures: one 2^log2_bits-bit stream decoded twice."""
     from paper_2011_09337_gb300 import synth
     K9, B9, P9 = synth.CODE_K9_R12
-    n = 1 << 25
+    n = 1 << log2_bits
     code = vit.Code(K9, B9, P9, f=2048, v=96)
 
     def enc(bits):
@@ -744,10 +756,12 @@ def main():
                          "(the target of the ncu captures)")
     ap.add_argument("--streams", type=int, default=len(EBN0))
     ap.add_argument("--profile-code", default="k7", choices=["k7", "k9", "frame", "probe", "metric"],
-                    help="with --profile: k7 = the batch above; k9 = one 2^25-bit K=9 (561,753) stream, "
+                    help="with --profile: k7 = the batch above; k9 = one K=9 (561,753) stream (--profile-log2-bits), "
                          "f=2048, v=96, decoded twice; frame = the single-frame latency case, decoded twice; "
                          "probe = the instruction-rate probes of the roofline peak, once each; metric = the "
                          "path-metric workload, forward and backward once per form")
+    ap.add_argument("--profile-log2-bits", type=int, default=25,
+                    help="with --profile --profile-code k9: the stream's size, 2^N info bits")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -767,7 +781,7 @@ def main():
 
     from paper_2011_09337_gb300 import vit
     if args.profile and args.profile_code == "k9":
-        profile_k9(vit, torch, dev)
+        profile_k9(vit, torch, dev, args.profile_log2_bits)
         return
     if args.profile and args.profile_code == "probe":
         print(json.dumps({"profile_run": "ok", "code": "probe", "int": alu_peak_leg(vit, dev),

@@ -269,6 +269,24 @@ def metric_workspace(code: Code, nframes: int, n: int, tau: float, C: int) -> in
     return int(load().vit_metric_workspace(code.handle, nframes, n, float(tau), C))
 
 
+def metric_fwd(code: Code, llr: torch.Tensor, tau: float, C: int, out: torch.Tensor, ws: torch.Tensor) -> None:
+    """vit_metric_fwd on caller-allocated tensors: llr float32 [F, n, beta],
+    out float32 [F], ws uint8 of at least metric_workspace(...) bytes (kept for
+    the matching metric_bwd)."""
+    F, n, _ = llr.shape
+    _check(load().vit_metric_fwd(code.handle, llr.data_ptr(), F, n, float(tau), C, out.data_ptr(),
+                                 ws.data_ptr(), ws.numel(), _stream(llr.device)))
+
+
+def metric_bwd(code: Code, llr: torch.Tensor, grad_metric: torch.Tensor, tau: float, C: int, ws: torch.Tensor,
+               grad_llr: torch.Tensor) -> None:
+    """vit_metric_bwd on caller-allocated tensors: grad_metric float32 [F],
+    grad_llr float32 [F, n, beta], ws as left by metric_fwd."""
+    F, n, _ = llr.shape
+    _check(load().vit_metric_bwd(code.handle, llr.data_ptr(), grad_metric.data_ptr(), F, n, float(tau), C,
+                                 ws.data_ptr(), ws.numel(), grad_llr.data_ptr(), _stream(llr.device)))
+
+
 class ViterbiMetric(torch.autograd.Function):
     """Best-path metric of zero-terminated frames (tau == 0) or its
     temperature-tau log-sum-exp relaxation (tau > 0), with a hand-written
@@ -285,8 +303,7 @@ class ViterbiMetric(torch.autograd.Function):
         F, n, _ = x.shape
         ws = torch.empty(max(metric_workspace(code, F, n, tau, C), 1), dtype=torch.uint8, device=x.device)
         out = torch.empty(F, dtype=torch.float32, device=x.device)
-        _check(load().vit_metric_fwd(code.handle, x.data_ptr(), F, n, float(tau), C, out.data_ptr(),
-                                     ws.data_ptr(), ws.numel(), _stream(x.device)))
+        metric_fwd(code, x, tau, C, out, ws)
         ctx.save_for_backward(x)
         ctx.ws, ctx.code, ctx.tau, ctx.C = ws, code, float(tau), C
         return out
@@ -294,11 +311,9 @@ class ViterbiMetric(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
         (x,) = ctx.saved_tensors
-        F, n, _ = x.shape
         g = grad_out.contiguous().to(torch.float32)
         grad = torch.empty_like(x)
-        _check(load().vit_metric_bwd(ctx.code.handle, x.data_ptr(), g.data_ptr(), F, n, ctx.tau, ctx.C,
-                                     ctx.ws.data_ptr(), ctx.ws.numel(), grad.data_ptr(), _stream(x.device)))
+        metric_bwd(ctx.code, x, g, ctx.tau, ctx.C, ctx.ws, grad)
         return grad, None, None, None
 
 
