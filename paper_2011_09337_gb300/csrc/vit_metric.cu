@@ -23,7 +23,9 @@
 // predecessor states (segment alphas in shared memory when they fit); the
 // per-stage gradient sums go through shared memory, one stage per lane, 32
 // stages at a time.  Each block's LLRs are loaded one block ahead, and each
-// stage's LLRs are shuffled out one stage ahead.
+// stage's LLRs are shuffled out one stage ahead.  The soft backward's two
+// stage loops are unrolled by four rather than 32 (its code then fits the
+// instruction cache: 0.49 against 0.56 ms on 1024 frames of 2054 stages).
 //
 // Log-sum-exp in base 2: tau log(e^{x/tau} + e^{y/tau}) = max(x, y) +
 // tau ln2 log2(1 + 2^{-|x - y| log2(e) / tau}), with the hardware base-2
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(32) metric_bwd_soft_kernel(const MArgs a) {
         const int cnt = (t1 - b < 32) ? (int)(t1 - b) : 32;
         float l[B];
         stage_llr<B>(lv, 0, l);
-        block_stages<false, (R <= 2)>(cnt, [&](int k) {
+        block_stages<false, false>(cnt, [&](int k) {
           const int64_t t = b + k;
 #pragma unroll
           for (int r = 0; r < R; r++)
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(32) metric_bwd_soft_kernel(const MArgs a) {
       float bmx = -INFINITY;
       float l[B];
       stage_llr<B>(lv, cnt - 1, l);
-      block_stages<true, (R <= 2)>(cnt, [&](int k) {
+      block_stages<true, false>(cnt, [&](int k) {
         const int64_t t = lo + k;
         float ln[B];  // the next (lower) stage's LLRs (lane -1 reads lane 31: unused)
         stage_llr<B>(lv, k - 1, ln);
