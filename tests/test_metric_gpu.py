@@ -139,3 +139,29 @@ def test_soft_gradient_small_tau(vit):
     assert np.all(np.isfinite(g))
     np.testing.assert_allclose(m, want_m, rtol=1e-5)
     np.testing.assert_allclose(g, want_g, rtol=1e-3, atol=2e-3)
+
+
+@pytest.mark.parametrize("code", [(3, 2, (0o7, 0o5)), (7, 2, (0o171, 0o133))], ids=["K3", "K7"])
+@pytest.mark.parametrize("n_info", [1, 9, 26, 40])
+@pytest.mark.parametrize("tau,C", [(0.0, 64), (1.0, 2), (1.0, 64)])
+def test_metric_short_frames(vit, code, n_info, tau, C):
+    # frames shorter than one 32-stage block, or just over one; checkpoint
+    # intervals below and above the frame length
+    k, beta, polys = code
+    _, llr = synth.float_frames(lambda x: oracle.encode(k, beta, polys, x), beta, k, 5, n_info, 1.5, seed=14)
+    c = vit.Code(k, beta, polys)
+    x = torch.from_numpy(llr).cuda().requires_grad_(True)
+    m = vit.path_metric(x, c, tau, C)
+    m.sum().backward()
+    torch.cuda.synchronize()
+    got_m = m.detach().cpu().numpy().astype(np.float64)
+    got_g = x.grad.cpu().numpy().astype(np.float64)
+    x64 = llr.astype(np.float64)
+    if tau == 0.0:
+        want_m, want_g = oracle.metric_hard(k, beta, polys, x64)
+        np.testing.assert_allclose(got_m, want_m, rtol=1e-5, atol=1e-4)
+        assert np.mean(got_g != want_g) < 2e-2
+    else:
+        want_m, want_g = oracle.metric_lse(k, beta, polys, x64, tau)
+        np.testing.assert_allclose(got_m, want_m, rtol=1e-5, atol=1e-4)
+        np.testing.assert_allclose(got_g, want_g, rtol=1e-3, atol=2e-4)
