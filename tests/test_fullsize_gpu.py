@@ -60,3 +60,71 @@ def test_benchmark_step_sampled_against_oracle(vit):
     torch.cuda.synchronize()
     for i in range(7):
         assert torch.equal(h_out[i], d_out[i].cpu()), f"stream {i}"
+
+
+def test_mixed_batch_full_size_sampled(vit):
+    # the benchmark's mixed batch: 4096 zero-terminated frames, info lengths
+    # U[40, 6144], half K=7 r1/3, half K=9 r1/2, Eb/N0 U[1, 5] dB, at the
+    # tilings its tuner settles on; one graph launch (concurrent per-code
+    # launches) and the persistent two-code launch, sampled frames against
+    # the oracle
+    spec = synth.mixed_batch_spec(4096, 2)
+    codes = [synth.CODE_K7_R13, synth.CODE_K9_R12]
+    tilings = {0: (256, 42), 1: (256, 80)}
+    cobj = {ci: vit.Code(*codes[ci], f=tilings[ci][0], v=tilings[ci][1], mode=vit.TERMINATED) for ci in (0, 1)}
+    dev = torch.device("cuda")
+    frames, specs = [], []
+    for fs in spec:
+        K, beta, polys = codes[fs.code]
+        n = fs.n_info + K - 1
+        s = synth.make_stream(lambda x, K=K, beta=beta, polys=polys: oracle.encode(K, beta, polys, x), beta, n,
+                              fs.ebn0_db, fs.seed, tail=K - 1)
+        x = torch.from_numpy(s.llr.reshape(-1)).to(dev)
+        o = torch.full(((cobj[fs.code].output_bits(n) + 7) // 8,), 0xAA, dtype=torch.uint8, device=dev)
+        frames.append((fs.code, n, s, o))
+        specs.append((cobj[fs.code], x, n, vit.TERMINATED, o))
+    g = synth.rng(21)
+    lens = np.array([n for _, n, _, _ in frames])
+    sample = np.unique(np.concatenate([[0, len(frames) - 1, int(lens.argmax()), int(lens.argmin())],
+                                       g.integers(0, len(frames), 40)]))
+    want = {}
+    for k in sample:
+        ci, n, s, _ = frames[k]
+        K, beta, polys = codes[ci]
+        f, v = tilings[ci]
+        want[k] = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v, oracle.TERMINATED)[: n - (K - 1)]
+    for persistent in (False, True):
+        for _, _, _, o in frames:
+            o.fill_(0xAA)
+        b = vit.Batch(specs, graph=True, persistent=persistent)
+        b.run()
+        b.run()
+        torch.cuda.synchronize()
+        for k in sample:
+            ci, n, _, o = frames[k]
+            got = synth.unpack_bits(o.cpu().numpy(), n - (codes[ci][0] - 1))
+            np.testing.assert_array_equal(got, want[k], err_msg=f"frame {k} code {ci} n={n} persistent={persistent}")
+
+
+def test_path_metric_full_size_sampled(vit):
+    # the benchmark's path-metric workload: 1024 frames x 2054 stages, K=7 r1/2,
+    # FP32 LLRs at 2 dB, C = 64; sampled frames against the FP64 oracle
+    _, llr = synth.float_frames(lambda x: oracle.encode(K, BETA, POLYS, x), BETA, K, 1024, 2048, 2.0, seed=3)
+    code = vit.Code(K, BETA, POLYS, mode=vit.TERMINATED)
+    sample = [0, 1, 511, 1023] + [int(i) for i in synth.rng(22).integers(0, 1024, 4)]
+    for tau in (0.0, 1.0):
+        x = torch.from_numpy(llr).cuda().requires_grad_(True)
+        m = vit.path_metric(x, code, tau, 64)
+        m.sum().backward()
+        torch.cuda.synchronize()
+        got_m = m.detach().cpu().numpy().astype(np.float64)[sample]
+        got_g = x.grad.cpu().numpy().astype(np.float64)[sample]
+        x64 = llr[sample].astype(np.float64)
+        if tau == 0.0:
+            want_m, want_g = oracle.metric_hard(K, BETA, POLYS, x64)
+            np.testing.assert_allclose(got_m, want_m, rtol=1e-5)
+            assert np.mean(got_g != want_g) < 1e-3
+        else:
+            want_m, want_g = oracle.metric_lse(K, BETA, POLYS, x64, tau)
+            np.testing.assert_allclose(got_m, want_m, rtol=1e-5)
+            np.testing.assert_allclose(got_g, want_g, rtol=1e-3, atol=2e-4)
