@@ -427,6 +427,32 @@ static const CodeEntry* tile_entry(const vit_code* c, int64_t n) {
   return (r > 0 && 4 * task_count(c->entry, tile_count(n, c->f)) <= r) ? c->spread : c->entry;
 }
 
+// CTA size of a single-frame tile-decoder launch of `tasks` warp tasks that
+// fits one wave.  The block scheduler deals CTAs to the SMs in turn, so when
+// kWarpsPerCta-warp CTAs do not divide evenly some SMs hold a CTA more than
+// others, and the launch lasts as long as its busiest SM.  One CTA of
+// ceil(tasks / SMs) warps per SM evens the load; larger CTAs cost ~2% by
+// themselves (the 7 x 2^24-bit K=7 batch, 12 warps on every SM either way:
+// 0.856 ms with 12-warp CTAs, 0.836 ms with 4), so they are taken when the
+// busiest SM loses at least 5% of its warps.  A 2^26-bit K=9 stream (2048
+// tasks on 152 SMs): 14-warp CTAs instead of 16 warps on some SMs, 2.77
+// against 3.03 ms.
+static int balanced_warps(const CodeEntry* e, int64_t tasks) {
+  int dev = 0, sms = 0;
+  if (e->resident == nullptr || tasks <= 0 || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return kWarpsPerCta;
+  }
+  const int64_t w = kWarpsPerCta;
+  const int64_t busiest = ((((tasks + w - 1) / w) + sms - 1) / sms) * w;
+  const int64_t wb = (tasks + sms - 1) / sms;
+  if (wb <= w || wb > kMaxCtaWarps || 100 * busiest < 105 * wb) return kWarpsPerCta;
+  // one such CTA must fit an SM (then the launch is one wave)
+  if (e->resident((int)wb) < (int64_t)sms * wb) return kWarpsPerCta;
+  return (int)wb;
+}
+
 // Slab slots of a single-frame decode with the tile decoder: 0 (one per
 // warp task) when every task's warp can be resident at once, else the
 // number of warps resident on the current device, which then stride over the
@@ -520,7 +546,8 @@ static int decode_impl(const vit_code* c, const int8_t* llr, int64_t n, uint8_t*
                   "traceback and a code with such a decoder", (int)kWarpSmemStages);
     launch = c->warp_launch;
   }
-  cudaError_t e = launch(a, kWarpsPerCta, s);
+  const int warps = (launch == te->launch && slots == 0) ? balanced_warps(te, tasks) : kWarpsPerCta;
+  cudaError_t e = launch(a, warps, s);
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   return VIT_OK;
 }

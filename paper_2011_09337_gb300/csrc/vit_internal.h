@@ -9,6 +9,7 @@
 namespace vit {
 
 constexpr int kWarpsPerCta = 4;   // default CTA size (warps)
+constexpr int kMaxCtaWarps = 32;  // largest CTA a launcher accepts (1024 threads)
 constexpr int kMaxRegs = 168;     // registers per thread of the tile decoders
 // Rotating-slot (K = 8, 9) decoders with word loads: 128 registers let 4
 // CTAs of 4 warps share an SM, so a 2^26-bit K=9 stream (2048 warp tasks)
@@ -214,7 +215,7 @@ struct MixEntry {
 // split).
 template <void (*kernel)(const KArgs)>
 cudaError_t launch_tasks(const KArgs& a, int warps, cudaStream_t s) {
-  if (warps < 1 || warps > 8) warps = kWarpsPerCta;
+  if (warps < 1 || warps > kMaxCtaWarps) warps = kWarpsPerCta;
   if (a.slots > 0) {  // at most `slots` warps stride over the tasks
     const int64_t need = a.ntasks - a.task_base < a.slots ? a.ntasks - a.task_base : a.slots;
     kernel<<<(unsigned)((need + warps - 1) / warps), warps * 32, 0, s>>>(a);

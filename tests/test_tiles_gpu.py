@@ -183,3 +183,19 @@ def test_slab_slots_reused_beyond_one_wave(vit, key):
     want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v)
     got = _decode(vit, key, s.llr, n, f, v, v, oracle.STREAM)
     np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("key,tasks", [("k7", 700), ("k9", 1000), ("k7r13", 1300)])
+def test_balanced_cta_launch(vit, key, tasks):
+    """Single frames whose warp tasks fill one wave unevenly with 4-warp CTAs
+    (on 152 SMs: 700 tasks -> 5-warp CTAs, 1000 K=9 tasks -> 7-warp CTAs,
+    1300 -> 9-warp CTAs) decode with one larger CTA per SM; every bit matches
+    the oracle."""
+    K, beta, polys = CODES[key]
+    f, v = 8, 2 * (K - 1)
+    tpt = 64 if K <= 7 else 16
+    n = f * tpt * tasks - 3  # the last task one tile short, the last tile ragged
+    s = synth.make_stream(_enc(CODES[key]), beta, n, 2.0, seed=40 + K)
+    want = oracle.viterbi_blocked(K, beta, polys, s.llr, f, v, v)
+    got = _decode(vit, key, s.llr, n, f, v, v, oracle.STREAM)
+    np.testing.assert_array_equal(got, want)
