@@ -50,6 +50,35 @@ __device__ __forceinline__ uint64_t spread_even(uint32_t x) {
   return v;
 }
 
+// Branch-metric multipliers of a lane's two predecessor branches per state:
+// delta = sum_b s[b] * l[b] with s[b] = -1 where the branch's output bit b is
+// 1 (Eq. 2).  When every generator taps the oldest input (the SYMMETRIC
+// codes), the branches from 2s and 2s + 1 carry complementary patterns and
+// the second delta is the negated first.
+template <class C>
+constexpr bool complementary_branches() {
+  if constexpr (C::GENERIC)
+    return false;  // generators known only at run time
+  else
+    return C::SYMMETRIC;
+}
+
+template <class C>
+struct WarpSigns {
+  static constexpr int R = C::S > 32 ? 2 : 1;
+  static constexpr bool kComplement = complementary_branches<C>();
+  int sA[R][C::BETA], sB[R][C::BETA];
+  __device__ __forceinline__ void init(const uint32_t (&cA)[R], const uint32_t (&cB)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+      for (int b = 0; b < C::BETA; b++) {
+        sA[r][b] = ((cA[r] >> b) & 1u) ? -1 : 1;
+        sB[r][b] = ((cB[r] >> b) & 1u) ? -1 : 1;
+      }
+  }
+};
+
 // One trellis stage (Eq. 3, Eq. 4) of the warp's tile: `pk` holds the
 // stage's LLR bytes, m the lane's metrics (states R*lane + r); returns the
 // ballot of each register's decisions.  Both predecessors 2s, 2s+1 (mod S)
@@ -57,16 +86,31 @@ __device__ __forceinline__ uint64_t spread_even(uint32_t x) {
 // R = 2, register 0 of lanes 2s and 2s+1 (mod S) when R = 1.  The metrics
 // stay far from 2^31 (windows of at most kWarpSmemStages stages), so the
 // survivor is a plain signed max and the decision compare is off the
-// metrics' dependency chain.
+// metrics' dependency chain.  The branch metrics depend only on the LLRs, so
+// they are formed before the metrics' shuffles and only one add per
+// candidate sits on the chain.
 template <class C>
 __device__ __forceinline__ void warp_stage(int (&m)[C::S > 32 ? 2 : 1], uint32_t pk, int lane, bool live,
-                                           const uint32_t (&cA)[C::S > 32 ? 2 : 1],
-                                           const uint32_t (&cB)[C::S > 32 ? 2 : 1], uint32_t (&bal)[2]) {
+                                           const WarpSigns<C>& sg, uint32_t (&bal)[2]) {
   constexpr int S = C::S;
   constexpr int R = S > 32 ? 2 : 1;
   int l[C::BETA];
 #pragma unroll
   for (int b = 0; b < C::BETA; b++) l[b] = (int)(int8_t)(uint8_t)(pk >> (8 * b));
+  int dA[R], dB[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    dA[r] = sg.sA[r][0] * l[0];
+#pragma unroll
+    for (int b = 1; b < C::BETA; b++) dA[r] += sg.sA[r][b] * l[b];
+    if constexpr (WarpSigns<C>::kComplement) {
+      dB[r] = -dA[r];
+    } else {
+      dB[r] = sg.sB[r][0] * l[0];
+#pragma unroll
+      for (int b = 1; b < C::BETA; b++) dB[r] += sg.sB[r][b] * l[b];
+    }
+  }
   int q0[R], q1[R];
   if constexpr (R == 2) {
 #pragma unroll
@@ -82,7 +126,7 @@ __device__ __forceinline__ void warp_stage(int (&m)[C::S > 32 ? 2 : 1], uint32_t
   bal[1] = 0u;
 #pragma unroll
   for (int r = 0; r < R; r++) {
-    const int x0 = q0[r] + warp_delta<C>(l, cA[r]), x1 = q1[r] + warp_delta<C>(l, cB[r]);
+    const int x0 = q0[r] + dA[r], x1 = q1[r] + dB[r];
     bal[r] = __ballot_sync(0xffffffffu, live && x1 > x0);  // ties keep the even predecessor
     m[r] = x1 > x0 ? x1 : x0;
   }
@@ -115,6 +159,8 @@ __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int l
     }
   }
   const bool live = R * lane < S;
+  WarpSigns<C> sg;
+  sg.init(cA, cB);
   const int8_t* llr = h.llr + h.t0 * C::BETA;
   // the stage word of lane l's kept ballots, bit s = state s
   auto word = [](uint32_t kA, uint32_t kB) -> uint64_t {
@@ -132,7 +178,7 @@ __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int l
 #pragma unroll
     for (int k = 0; k < 32; k++) {
       uint32_t bal[2];
-      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), lane, live, cA, cB, bal);
+      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), lane, live, sg, bal);
       kA = lane == k ? bal[0] : kA;
       kB = lane == k ? bal[1] : kB;
     }
@@ -143,7 +189,7 @@ __device__ void decode_tile_warp(const Half& h, uint32_t M, uint64_t* dec, int l
     uint32_t kA = 0u, kB = 0u;
     for (int k = 0; k < L - i0; k++) {
       uint32_t bal[2];
-      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), lane, live, cA, cB, bal);
+      warp_stage<C>(m, __shfl_sync(0xffffffffu, cur, k), lane, live, sg, bal);
       kA = lane == k ? bal[0] : kA;
       kB = lane == k ? bal[1] : kB;
     }
