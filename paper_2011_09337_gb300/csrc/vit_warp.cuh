@@ -19,15 +19,6 @@
 namespace vit {
 
 #if defined(__CUDACC__)
-// Signed branch metric of pattern c for this stage's LLRs (Eq. 2).
-template <class C>
-__device__ __forceinline__ int warp_delta(const int (&l)[C::BETA], uint32_t c) {
-  int d = 0;
-#pragma unroll
-  for (int b = 0; b < C::BETA; b++) d += ((c >> b) & 1u) ? -l[b] : l[b];
-  return d;
-}
-
 // The beta LLR bytes of window iteration i (bytes of one 32-bit word).
 template <class C>
 __device__ __forceinline__ uint32_t warp_llr_word(const int8_t* llr, int i, int L) {
@@ -264,13 +255,18 @@ __device__ void decode_tile_warp_gen(const Half& h, uint32_t M, uint32_t* dec, i
   const int L = (int)(h.t1 - h.t0);
   const bool live = R * lane < S;
   int m[R];
-  uint32_t cA[R], cB[R];
+  int sA[R][C::BETA], sB[R][C::BETA];  // branch-metric multipliers (Eq. 2) of the branches from 2s and 2s + 1
 #pragma unroll
   for (int r = 0; r < R; r++) {
     const int j = R * lane + r;
     m[r] = (h.known && j != 0) ? -(int)M : 0;
-    cA[r] = aout_rt(polys, C::BETA, 2u * (uint32_t)j);
-    cB[r] = aout_rt(polys, C::BETA, 2u * (uint32_t)j + 1u);
+    const uint32_t cA = aout_rt(polys, C::BETA, 2u * (uint32_t)j);
+    const uint32_t cB = aout_rt(polys, C::BETA, 2u * (uint32_t)j + 1u);
+#pragma unroll
+    for (int b = 0; b < C::BETA; b++) {
+      sA[r][b] = ((cA >> b) & 1u) ? -1 : 1;
+      sB[r][b] = ((cB >> b) & 1u) ? -1 : 1;
+    }
   }
   const int8_t* llr = h.llr + h.t0 * C::BETA;
   const int la = (2 * lane) & (R == 1 ? S - 1 : 31), lb = (2 * lane + 1) & (R == 1 ? S - 1 : 31);
@@ -287,6 +283,17 @@ __device__ void decode_tile_warp_gen(const Half& h, uint32_t M, uint32_t* dec, i
       int l[C::BETA];
 #pragma unroll
       for (int b = 0; b < C::BETA; b++) l[b] = (int)(int8_t)(uint8_t)(pk >> (8 * b));
+      int dA[R], dB[R];  // branch metrics, formed before the metrics' shuffles
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        dA[r] = sA[r][0] * l[0];
+        dB[r] = sB[r][0] * l[0];
+#pragma unroll
+        for (int b = 1; b < C::BETA; b++) {
+          dA[r] += sA[r][b] * l[b];
+          dB[r] += sB[r][b] * l[b];
+        }
+      }
       int qa[R], qb[R];
 #pragma unroll
       for (int r = 0; r < R; r++) {
@@ -303,7 +310,7 @@ __device__ void decode_tile_warp_gen(const Half& h, uint32_t M, uint32_t* dec, i
           p0 = (2 * r < R) ? qa[2 * r] : qb[2 * r - R];
           p1 = (2 * r < R) ? qa[2 * r + 1] : qb[2 * r - R + 1];
         }
-        const int x0 = p0 + warp_delta<C>(l, cA[r]), x1 = p1 + warp_delta<C>(l, cB[r]);
+        const int x0 = p0 + dA[r], x1 = p1 + dB[r];
         const uint32_t bal = __ballot_sync(0xffffffffu, live && x1 > x0);  // ties keep the even predecessor
         keep[r] = (lane == k) ? bal : keep[r];
         m[r] = x1 > x0 ? x1 : x0;
