@@ -261,7 +261,9 @@ int vit_decode_batch(const vit_frame* frames, int nframes, vit_stream_t stream);
  * llr: device float32 [F][n][beta]; metric_out: device float32 [F].
  * ws: device scratch of vit_metric_workspace(...) bytes, kept unchanged
  * between vit_metric_fwd and the matching vit_metric_bwd (it holds the
- * survivor bits, or the forward state metrics every C stages).
+ * survivor bits, or the forward state metrics every C stages with their fp64
+ * offsets and the forward metric, which the backward uses as the common scale
+ * of each stage's posteriors).
  */
 size_t vit_metric_workspace(const vit_code* code, int nframes, int64_t n, float tau, int C);
 int vit_metric_fwd(const vit_code* code, const float* llr, int nframes, int64_t n, float tau, int C,
