@@ -231,7 +231,7 @@ __device__ __forceinline__ void block_stages(int cnt, F&& body) {
 }
 
 template <int R, int B, bool SOFT>
-__global__ void __launch_bounds__(kWarps * 32) metric_fwd_kernel(const MArgs a) {
+__global__ void __launch_bounds__(SOFT ? kWarps * 32 : 32) metric_fwd_kernel(const MArgs a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int f = blockIdx.x * (blockDim.x >> 5) + w;
   if (f >= a.F) return;
@@ -625,9 +625,9 @@ template <int R, int B>
 void launch_rb(int which, bool soft, const MArgs& a, cudaStream_t s) {
   const unsigned grid = (unsigned)((a.F + kWarps - 1) / kWarps);
   if (which == 0) {
-    // the hard forward one frame per CTA (1024 frames: 87.5 against 91.9 us
-    // with 4-frame CTAs, which leave some SMs 8 warps and others 4); the
-    // soft forward measured 1% slower that way
+    // the hard forward one frame per CTA, compiled for 32-thread CTAs
+    // (1024 frames: 87.4 against 91.7 us with 4-frame CTAs); the soft
+    // forward measured 1% slower that way
     if (soft)
       metric_fwd_kernel<R, B, true><<<grid, kWarps * 32, 0, s>>>(a);
     else
