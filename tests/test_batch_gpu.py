@@ -52,7 +52,17 @@ def test_mixed_codes_one_launch(vit, tiling):
         b = vit.Batch(specs, graph=True, warps=warps, persistent=persistent)
         b.run()
         b.run()  # replay of the captured graph
+        # a copy queued right behind the batch on the same stream must see
+        # every group's output (the groups after the first are launched as
+        # programmatic dependents): clear, run, copy, with no sync between
         torch.cuda.synchronize()
+        want_all = torch.cat(outs)
+        for o in outs:
+            o.fill_(0xAA)
+        b.run()
+        snap = torch.cat(outs)
+        torch.cuda.synchronize()
+        assert torch.equal(snap, want_all), (warps, persistent)
         for k, (ci, n, s) in enumerate(frames):
             K, beta, polys = codes[ci]
             f, v = tiling[ci]
