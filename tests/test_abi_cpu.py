@@ -199,3 +199,28 @@ def test_parallel_traceback_setter_checks(lib):
     assert rc == 0
     assert f(h, 32, 0, 0) == -2 and b"parallel-traceback" in lib.vit_last_error()
     lib.vit_destroy(h)
+
+
+def test_metric_workspace_layout(lib):
+    """vit_metric_workspace per frame: hard form = n stages x ceil(S/32)
+    decision words; log-sum-exp form = (checkpoints + C segment rows) x S
+    floats, then one fp64 offset per checkpoint and the forward metric; each
+    frame's share rounded to 256 bytes; invalid arguments give 0."""
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.vit_metric_workspace.argtypes = [vp, ctypes.c_int, i64, ctypes.c_float, ctypes.c_int]
+    lib.vit_metric_workspace.restype = ctypes.c_size_t
+    up = lambda x: (x + 255) // 256 * 256
+    for K, polys in ((7, (0o171, 0o133)), (9, (0o561, 0o753)), (4, (0o13, 0o15))):
+        rc, h = _create(lib, K, 2, polys, 0, 0)
+        assert rc == 0
+        S = 1 << (K - 1)
+        n, F = 2054, 3
+        assert lib.vit_metric_workspace(h, F, n, 0.0, 64) == F * up(n * ((S + 31) // 32) * 4)
+        for C in (2, 7, 64, 4096):
+            nck = (n + C - 1) // C
+            assert lib.vit_metric_workspace(h, F, n, 1.0, C) == F * up((nck + C) * S * 4 + (nck + 1) * 8)
+        assert lib.vit_metric_workspace(h, F, n, 1.0, 1) == 0       # C below 2
+        assert lib.vit_metric_workspace(h, F, n, -1.0, 64) == 0     # negative tau
+        assert lib.vit_metric_workspace(h, 0, n, 1.0, 64) == 0      # no frames
+        assert lib.vit_metric_workspace(h, F, K - 1, 1.0, 64) == 0  # shorter than K stages
+        lib.vit_destroy(h)
